@@ -1,0 +1,617 @@
+"""Pins of the CPU oracle against facts fixed outside it: the paper's worked
+example (Fig. 4), axis-aligned geometry, library routines, brute force on tiny
+maps, closed forms and invariants stated in the paper."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1705_01167_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_fig4():
+    grid, lut, cur = [], [], None
+    with open(os.path.join(GOLDEN, "fig4_theta0.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line in ("grid", "lut_theta0"):
+                cur = grid if line == "grid" else lut
+                continue
+            cur.append(line.split())
+    g = np.array([[int(v) for v in r] for r in grid], np.uint8)
+    return g, lut
+
+
+def _tiny_maps(n_maps=6, seed=11):
+    rs = synth.Stream(seed)
+    out = []
+    for m in range(n_maps):
+        W = int(rs.integers(1, 5, 20)[0])
+        H = int(rs.integers(1, 5, 20)[0])
+        dens = rs.uniform(1, 0.05, 0.45)[0]
+        g = (rs.uniform(W * H) < dens).astype(np.uint8).reshape(H, W)
+        out.append(g)
+    # a map with a solid 3x3 block (interior cell that is not an edge)
+    g = np.zeros((9, 11), np.uint8)
+    g[3:6, 4:7] = 1
+    out.append(g)
+    return out
+
+
+def _grid_states(W, H, N):
+    th = np.array([np.float32(2.0 * math.pi * k / N) for k in range(N)], np.float32)
+    jj, ii, kk = np.meshgrid(np.arange(H), np.arange(W), np.arange(N), indexing="ij")
+    return np.stack([ii.ravel(), jj.ravel(), th[kk.ravel()]], 1).astype(np.float32)
+
+
+def _random_queries(W, H, n, seed):
+    rs = synth.Stream(seed)
+    x = rs.uniform(n, -0.7, W - 0.3)
+    y = rs.uniform(n, -0.7, H - 0.3)
+    th = rs.uniform(n, -7.0, 14.0)
+    return np.stack([x, y, th], 1).astype(np.float32)
+
+
+# ------------------------------------------------------------------ Fig. 4
+
+def test_fig4_worked_example(oracle):
+    """Fig. 4: the theta = 0 LUT slice of the 4x4 example, cast at cell centres."""
+    g, lut = _read_fig4()
+    max_range = 100.0
+    d = oracle.OracleCDDT(g, 8, max_range)
+    poses = np.array([[i, j, 0.0] for j in range(4) for i in range(4)], np.float32)
+    want = np.array([[max_range if v == "-" else float(v) for v in row] for row in lut], np.float32)
+    np.testing.assert_array_equal(d.calc_range(poses).reshape(4, 4), want)
+    np.testing.assert_array_equal(d.params.calc_range_brute(g, poses).reshape(4, 4), want)
+    # the same slice from the 16-bit variant: the zero points are integers
+    d16 = oracle.OracleCDDT(g, 8, max_range, u16=True)
+    np.testing.assert_array_equal(d16.calc_range(poses).reshape(4, 4), want)
+
+
+# ------------------------------------------------------------------ edge map
+
+def test_edge_map_is_map_minus_erosion(oracle):
+    """Section IV-A: edge_map = map - erosion(map), 3x3 structuring element,
+    off-map cells count as free (scipy's binary erosion, border_value=0)."""
+    from scipy import ndimage
+    rs = synth.Stream(5)
+    for _ in range(5):
+        g = (rs.uniform(40 * 33) < 0.6).astype(np.uint8).reshape(33, 40)
+        er = ndimage.binary_erosion(g.astype(bool), structure=np.ones((3, 3), bool), border_value=0)
+        want = (g.astype(bool) & ~er).astype(np.uint8)
+        np.testing.assert_array_equal(oracle.edge_map(g), want)
+
+
+# ------------------------------------------------------------------ O1 == O2
+
+@pytest.mark.parametrize("u16", [False, True])
+def test_plain_cddt_equals_brute_force(oracle, u16):
+    """The stored, sorted, binary-searched CDDT (O2) answers every grid state
+    and random continuous queries exactly as the definition scanned over all
+    edge cells (O1)."""
+    for mi, g in enumerate(_tiny_maps()):
+        H, W = g.shape
+        for N in (4, 8, 12, 16):
+            d = oracle.OracleCDDT(g, N, 37.5, u16=u16)
+            q = np.concatenate([_grid_states(W, H, N), _random_queries(W, H, 800, 100 + mi)])
+            np.testing.assert_array_equal(d.calc_range(q), d.params.calc_range_brute(g, q))
+
+
+def test_lut_equals_cddt_at_grid_states(oracle):
+    """O4 (a lookup table of every discrete state, Section II) read at each
+    state equals the CDDT cast from that state."""
+    g = _tiny_maps()[2]
+    H, W = g.shape
+    N = 12
+    d = oracle.OracleCDDT(g, N, 50.0)
+    lut = d.params.lut(g)
+    assert lut.shape == (N, H, W)
+    q = _grid_states(W, H, N)  # ordered (j, i, k)
+    got = d.calc_range(q).reshape(H, W, N).transpose(2, 0, 1)
+    np.testing.assert_array_equal(got, lut)
+
+
+def test_lut_memory_closed_forms():
+    """Reading S1 (N directions span the full circle) reproduces the paper's
+    lookup-table sizes at 16 bits per entry: 1000^2 x 108 x 2 B = 216 MB
+    (Table I) and 2000^2 x 200 x 2 B > 1.5 GB (Section I)."""
+    assert 1000 * 1000 * 108 * 2 == 216_000_000
+    assert 2000 * 2000 * 200 * 2 > 1.5e9
+    assert 4000 * 4000 * 200 * 2 > 6e9
+
+
+# ------------------------------------------------------------------ axis-aligned
+
+def _walk(g, i, j, di, dj):
+    """First occupied cell from (i, j) stepping by (di, dj), or None."""
+    H, W = g.shape
+    while True:
+        i += di
+        j += dj
+        if not (0 <= i < W and 0 <= j < H):
+            return None
+        if g[j, i]:
+            return i, j
+
+
+@pytest.mark.parametrize("N", [8, 108, 200])
+def test_axis_aligned_rays_are_exact(oracle, N):
+    """At theta = 0, pi/2, pi, 3pi/2 a CDDT range is exactly the distance from
+    the query to the centre of the first occupied cell along the axis
+    (Section III's d_ray with the cell centre as the collision point), and a
+    query in an occupied cell returns 0 (Section IV-C pre-check)."""
+    g = synth.rect_map(64, 48, n_rects=12, seed=21)
+    H, W = g.shape
+    mr = 300.0
+    d = oracle.OracleCDDT(g, N, mr)
+    rs = synth.Stream(22)
+    n = 3000
+    ci = rs.integers(n, 0, W - 1)
+    cj = rs.integers(n, 0, H - 1)
+    fx = rs.uniform(n, -0.499, 0.499)
+    fy = rs.uniform(n, -0.499, 0.499)
+    dirs = [(0.0, 1, 0), (math.pi / 2, 0, 1), (math.pi, -1, 0), (3 * math.pi / 2, 0, -1)]
+    for th, di, dj in dirs:
+        q = np.stack([ci + fx, cj + fy, np.full(n, th)], 1).astype(np.float32)
+        got = d.calc_range(q)
+        for t in range(n):
+            x, y = q[t, 0], q[t, 1]
+            i, j = int(ci[t]), int(cj[t])
+            if g[j, i]:
+                assert got[t] == 0.0
+                continue
+            hit = _walk(g, i, j, di, dj)
+            if hit is None:
+                want = np.float32(mr)
+            elif di:
+                want = np.float32(hit[0]) - x if di > 0 else x - np.float32(hit[0])
+            else:
+                want = np.float32(hit[1]) - y if dj > 0 else y - np.float32(hit[1])
+            assert got[t] == min(want, np.float32(mr)), (th, x, y, got[t], want)
+
+
+def test_max_range_clamp(oracle):
+    """Ranges are clamped to max_range (Section III's ray cast up to the sensor
+    limit): with a short limit every axis-aligned range equals
+    min(distance to the first wall centre, max_range)."""
+    g = synth.rect_map(64, 64, n_rects=6, seed=23)
+    mr = 6.0
+    d = oracle.OracleCDDT(g, 16, mr)
+    q = np.array([[i, j, 0.0] for j in range(64) for i in range(64) if not g[j, i]], np.float32)
+    r = d.calc_range(q)
+    assert np.all(r <= np.float32(mr))
+    for t in range(q.shape[0]):
+        i, j = int(q[t, 0]), int(q[t, 1])
+        hit = _walk(g, i, j, 1, 0)
+        want = mr if hit is None else min(float(hit[0] - i), mr)
+        assert r[t] == np.float32(want)
+    assert np.mean(r == np.float32(mr)) > 0.2
+
+
+def test_sawtooth_rows(oracle):
+    """Section IV: along a row of the theta = 0 slice the distance grows by
+    exactly one per cell and drops to zero at an obstacle (Fig. 5)."""
+    g = synth.rect_map(80, 60, n_rects=15, seed=31)
+    H, W = g.shape
+    d = oracle.OracleCDDT(g, 108, 1000.0)
+    q = np.array([[i, j, 0.0] for j in range(H) for i in range(W)], np.float32)
+    r = d.calc_range(q).reshape(H, W)
+    for j in range(H):
+        for i in range(W - 1):
+            if g[j, i]:
+                assert r[j, i] == 0
+            elif g[j, i + 1]:
+                assert r[j, i] == 1
+            else:
+                assert r[j, i] == r[j, i + 1] + 1
+
+
+def test_empty_map_and_occupied_cells(oracle):
+    """An empty map has no zero points: every in-map query returns max_range.
+    A query inside an occupied cell, or off the map, returns 0."""
+    g = np.zeros((30, 40), np.uint8)
+    for u16 in (False, True):
+        d = oracle.OracleCDDT(g, 36, 123.0, u16=u16)
+        assert d.total_zp == 0
+        q = _random_queries(40, 30, 2000, 3)
+        inside = (np.floor(q[:, 0] + np.float32(0.5)) >= 0) & (np.floor(q[:, 0] + np.float32(0.5)) < 40) \
+            & (np.floor(q[:, 1] + np.float32(0.5)) >= 0) & (np.floor(q[:, 1] + np.float32(0.5)) < 30)
+        r = d.calc_range(q)
+        assert np.all(r[inside] == np.float32(123.0))
+        assert np.all(r[~inside] == 0.0)
+    g = synth.rect_map(50, 50, n_rects=8, seed=4)
+    d = oracle.OracleCDDT(g, 24, 80.0)
+    jj, ii = np.nonzero(g)
+    th = synth.Stream(6).uniform(ii.size, 0, 2 * math.pi)
+    q = np.stack([ii + 0.3, jj - 0.2, th], 1).astype(np.float32)
+    assert np.all(d.calc_range(q) == 0.0)
+
+
+def test_theta_wraps(oracle):
+    """theta and theta + 2 pi m name the same discrete direction."""
+    g = synth.rect_map(60, 60, n_rects=10, seed=8)
+    d = oracle.OracleCDDT(g, 60, 200.0)
+    N = 60
+    ks = np.arange(N)
+    th = np.array([np.float32(2 * math.pi * k / N) for k in ks], np.float32)
+    assert [d.params.query_k(t) for t in th] == list(ks)
+    # a direction just below / above the half-way point between two slices
+    step = 2 * math.pi / N
+    assert d.params.query_k(np.float32(0.49 * step)) == 0
+    assert d.params.query_k(np.float32(0.51 * step)) == 1
+    assert d.params.query_k(np.float32(-0.49 * step)) == 0
+    assert d.params.query_k(np.float32(-0.51 * step)) == N - 1
+    rs = synth.Stream(9)
+    n = 2000
+    q = _random_queries(60, 60, n, 10)
+    q[:, 2] = rs.uniform(n, 0.001, 2 * math.pi - 0.001)
+    # keep directions away from the rounding boundary so the float32 shift
+    # by 2 pi cannot move them across it
+    frac = (q[:, 2] * N / (2 * math.pi)) % 1.0
+    q = q[np.abs(frac - 0.5) > 1e-3]
+    q2 = q.copy()
+    q2[:, 2] = q[:, 2] + np.float32(2 * math.pi)
+    q3 = q.copy()
+    q3[:, 2] = q[:, 2] - np.float32(2 * math.pi)
+    r = d.calc_range(q)
+    np.testing.assert_array_equal(r, d.calc_range(q2))
+    np.testing.assert_array_equal(r, d.calc_range(q3))
+
+
+# ------------------------------------------------------------------ symmetry, pairing
+
+def test_half_storage_matches_full_circle(oracle):
+    """Section IV-C: one set of zero points answers theta and theta + pi; the
+    half-storage CDDT with a backward search equals a CDDT that stores all N
+    directions, on every query not within 1e-4 of a bin edge."""
+    g = synth.rect_map(70, 50, n_rects=14, seed=41)
+    H, W = g.shape
+    N = 36
+    half = oracle.OracleCDDT(g, N, 150.0)
+    full = oracle.OracleCDDT(g, N, 150.0, full=True)
+    ph, pf = half.params, full.params
+    # the stored tables of directions s and s + N/2 are exact negations
+    S = N // 2
+    exact = np.array([pf.c[s + S] == -ph.c[s] and pf.s[s + S] == -ph.s[s] for s in range(S)])
+    q = _random_queries(W, H, 20000, 42)
+    k = np.array([ph.query_k(t) for t in q[:, 2]])
+    s = k % S
+    yr = q[:, 1] * ph.c[s] - q[:, 0] * ph.s[s]
+    away = np.abs((yr % 1.0) - 0.5) > 1e-4
+    sel = away & exact[s]
+    assert sel.sum() > 10000
+    np.testing.assert_array_equal(half.calc_range(q[sel]), full.calc_range(q[sel]))
+
+
+def test_radial_pairing(oracle):
+    """Section IV-C and VI: with a 270-degree, 61-beam scan, beams i and i + 40
+    point opposite ways; when their slices coincide the backward answer sits at
+    index i - 1 of the forward search, and 21 pairs leave 40 traversals,
+    'a third' fewer than 61."""
+    B = 61
+    bo = synth.beam_offsets(B, 270.0)
+    D = synth.pair_offset(B, 270.0)
+    assert D == 40
+    assert abs((float(bo[D]) - float(bo[0])) - math.pi) < 1e-6
+    g = synth.rect_map(128, 128, n_rects=20, seed=51)
+    d = oracle.OracleCDDT(g, 108, 300.0)
+    parts = synth.uniform_particles(g, 400, seed=52)
+    trav = np.array([d.params.traversals(t, bo, D) for t in parts[:, 2]])
+    assert trav.min() >= 40 and trav.max() <= B
+    assert np.mean(trav == 40) > 0.6
+    assert abs(1.0 - np.mean(trav) / B - 1.0 / 3.0) < 0.03
+    # index relation of Section IV-C on every valid pair
+    ths = (parts[:, 2:3] + bo[None, :]).astype(np.float32)
+    q = np.concatenate([np.repeat(parts[:, :2], B, 0), ths.reshape(-1, 1)], 1)
+    r, kb, zi, sl, b = d.calc_range_info(q)
+    r, kb, zi, sl = (a.reshape(-1, B) for a in (r, kb, zi, sl))
+    checked = 0
+    for p in range(parts.shape[0]):
+        for i in range(B - D):
+            ki = d.params.query_k(ths[p, i])
+            kj = d.params.query_k(ths[p, i + D])
+            if kj != (ki + 54) % 108 or kb[p, i] < 0:
+                continue
+            f, r_ = (i, i + D) if ki < 54 else (i + D, i)
+            ub = zi[p, f] if zi[p, f] >= 0 else kb[p, f]
+            assert zi[p, r_] == ub - 1
+            checked += 1
+    assert checked > 4000
+
+
+# ------------------------------------------------------------------ approximation
+
+def test_against_exact_caster(oracle):
+    """The CDDT is an approximation (Section II, III).  At a discrete direction
+    a cell counts as hit when its rotated square meets the query's bin, a
+    superset of the cells the exact ray crosses, so (a) no ray leaks: the CDDT
+    range never exceeds the exact cast to the first crossed cell's centre by
+    more than half a cell (the centre-ordering slack), and (b) no hit is
+    invented: the reported collision point lies within 1 + h of the centre of
+    an occupied cell, h = (|cos| + |sin|)/2 the half-extent of a rotated cell."""
+    g = synth.rect_map(128, 128, n_rects=25, seed=61)
+    H, W = g.shape
+    N, mr = 108, 500.0
+    d = oracle.OracleCDDT(g, N, mr)
+    parts = synth.uniform_particles(g, 5000, seed=62)
+    ks = synth.Stream(63).integers(parts.shape[0], 0, N - 1)
+    th = np.array([np.float32(2 * math.pi * k / N) for k in ks], np.float32)
+    q = parts.copy()
+    q[:, 2] = th
+    r = d.calc_range(q).astype(np.float64)
+    ang = 2 * math.pi * ks / N
+    ex = oracle.cast_exact(g, np.stack([q[:, 0], q[:, 1], ang], 1), mr, 0)
+    assert np.all(r <= ex + 0.5 + 1e-4)
+    assert np.mean(np.abs(r - ex) < 1e-3) > 0.3
+    occ = np.argwhere(g)  # (row, col)
+    h = 0.5 * (np.abs(np.cos(ang)) + np.abs(np.sin(ang)))
+    hit = r < mr
+    assert hit.mean() > 0.99
+    px = q[:, 0] + r * np.cos(ang)
+    py = q[:, 1] + r * np.sin(ang)
+    for t in np.flatnonzero(hit):
+        dd = np.min(np.hypot(occ[:, 1] - px[t], occ[:, 0] - py[t]))
+        assert dd < 1.0 + h[t] + 1e-3, (t, dd)
+
+
+# ------------------------------------------------------------------ 16-bit
+
+def test_u16_quantisation(oracle):
+    """Reading S7: 16-bit zero points change a range by at most 1/(2Q) when the
+    same obstacle is hit; Q is the largest power of two with
+    (diag + 4) Q <= 65535."""
+    g = synth.rect_map(256, 256, n_rects=40, seed=71)
+    d32 = oracle.OracleCDDT(g, 108, 300.0)
+    d16 = oracle.OracleCDDT(g, 108, 300.0, u16=True)
+    diag = math.hypot(256, 256)
+    Q = d16.params.Q
+    assert Q == 2 ** math.floor(math.log2(65535 / (diag + 4)))
+    assert (diag + 4) * Q <= 65535 < (diag + 4) * 2 * Q
+    q = synth.uniform_particles(g, 20000, seed=72)
+    r32, kb32, zi32, _, _ = d32.calc_range_info(q)
+    r16, kb16, zi16, _, _ = d16.calc_range_info(q)
+    same = (zi32 == zi16) & (kb32 == kb16) & (zi32 >= 0) & (r32 < 300.0)
+    assert same.mean() > 0.95
+    assert np.max(np.abs(r32[same] - r16[same])) <= 0.5 / Q + 1e-4
+    assert d16.total_zp == d32.total_zp
+
+
+# ------------------------------------------------------------------ prune
+
+def test_prune_changes_no_answer(oracle):
+    """Section IV-C pruning (reading S8) removes zero points without changing
+    the answer of any query from a free cell: every grid state and random
+    continuous free-space queries."""
+    for seed, (W, H, N) in [(81, (40, 30, 16)), (82, (64, 64, 36))]:
+        g = synth.rect_map(W, H, n_rects=10, seed=seed)
+        full = oracle.OracleCDDT(g, N, 200.0)
+        pr = oracle.OracleCDDT(g, N, 200.0)
+        removed = pr.prune()
+        assert removed > 0
+        assert pr.total_zp == full.total_zp - removed
+        q = np.concatenate([_grid_states(W, H, N), _random_queries(W, H, 100000, seed + 1)])
+        np.testing.assert_array_equal(pr.calc_range(q), full.calc_range(q))
+        assert pr.prune() == -1
+
+
+def test_prune_interior_of_straight_wall(oracle):
+    """Section IV-C's example: in the theta = 0 slice the middle cells of a
+    line of obstacles along x are never hit, only its two ends."""
+    g = np.zeros((11, 21), np.uint8)
+    g[5, 3:18] = 1
+    d = oracle.OracleCDDT(g, 8, 100.0)
+    bs0, zp0 = d.export()
+    b = 5 + int(d.params.T[0])  # row 5 of slice 0
+    assert bs0[b + 1] - bs0[b] == 15
+    d.prune()
+    bs, zp = d.export()
+    np.testing.assert_array_equal(zp[bs[b]:bs[b + 1]], np.array([3.0, 17.0], np.float32))
+
+
+def test_prune_single_bin_agrees(oracle):
+    """The per-bin form of the pruning rule (all free cells scanned for one
+    bin) agrees with the whole-map pass."""
+    g = synth.rect_map(48, 40, n_rects=9, seed=91)
+    d = oracle.OracleCDDT(g, 20, 100.0)
+    bs, zp = d.export()
+    eps = oracle.prune_eps(48, 40)
+    keep_ref = []
+    sb = d.params.sbase
+    rs = synth.Stream(92)
+    picks = rs.integers(40, 0, d.params.total_bins - 1)
+    for gb in picks:
+        sl = int(np.searchsorted(sb, gb, side="right") - 1)
+        b = int(gb - sb[sl])
+        keep_ref.append((gb, d.params.prune_bin(g, sl, b, zp[bs[gb]:bs[gb + 1]], eps)))
+    d.prune(eps)
+    bs2, zp2 = d.export()
+    for gb, keep in keep_ref:
+        np.testing.assert_array_equal(zp2[bs2[gb]:bs2[gb + 1]], zp[bs[gb]:bs[gb + 1]][keep])
+
+
+# ------------------------------------------------------------------ update
+
+@pytest.mark.parametrize("u16", [False, True])
+def test_update_equals_rebuild(oracle, u16):
+    """Section IV-D: after any sequence of cell writes the incrementally updated
+    CDDT holds exactly the zero points of a CDDT built from the final map,
+    including obstacles revealed or hidden by the erosion."""
+    g = synth.rect_map(48, 36, n_rects=10, seed=101)
+    d = oracle.OracleCDDT(g, 24, 100.0, u16=u16)
+    rs = synth.Stream(102)
+    cur = g.copy()
+    for step in range(4):
+        n = 60
+        xy = np.stack([rs.integers(n, 0, 47), rs.integers(n, 0, 35)], 1).astype(np.int32)
+        occ = (rs.uniform(n) < 0.5).astype(np.uint8)
+        # a block write and clear exercises neighbour reveal
+        if step == 1:
+            blk = np.array([(x, y) for y in range(10, 15) for x in range(20, 26)], np.int32)
+            xy = np.concatenate([xy, blk])
+            occ = np.concatenate([occ, np.ones(len(blk), np.uint8)])
+        if step == 2:
+            blk = np.array([(x, y) for y in range(11, 14) for x in range(21, 25)], np.int32)
+            xy = np.concatenate([xy, blk])
+            occ = np.concatenate([occ, np.zeros(len(blk), np.uint8)])
+        assert d.update(xy, occ) == 0
+        for (x, y), o in zip(xy, occ):
+            cur[y, x] = o
+        ref = oracle.OracleCDDT(cur, 24, 100.0, u16=u16)
+        bs, zp = d.export()
+        bs_r, zp_r = ref.export()
+        np.testing.assert_array_equal(bs, bs_r)
+        np.testing.assert_array_equal(zp, zp_r)
+        gg, ee = d.grid_edge()
+        np.testing.assert_array_equal(gg, cur)
+        np.testing.assert_array_equal(ee, oracle.edge_map(cur))
+    d.prune()
+    assert d.update(np.zeros((1, 2), np.int32), np.ones(1, np.uint8)) == -1
+
+
+# ------------------------------------------------------------------ beam model
+
+def _model(oracle, mr=300.0, **kw):
+    base = dict(z_hit=0.0, z_short=0.0, z_max=0.0, z_rand=0.0, sigma_hit=8.0,
+                lambda_short=0.01, hit_truncnorm=0)
+    base.update(kw)
+    return oracle.beam_model(mr, **base)
+
+
+def test_beam_model_components(oracle):
+    """Beam model (Probabilistic Robotics): p_hit is the normal density
+    N(z; z*, sigma^2) (scipy), its truncated form integrates to 1 on
+    [0, z_max], p_short integrates to 1 on [0, z*], p_rand to 1 on
+    [0, z_max), p_max is a point mass at z_max, and the mixture is the
+    weighted sum with the weights unnormalised (they sum to 0.95)."""
+    from scipy import integrate, stats
+    mr = 300.0
+    zs_list = [0.0, 0.5, 3.0, 40.0, 150.0, 299.0]
+    z = np.linspace(0, mr, 30001)
+    for zs in zs_list:
+        p, _ = oracle.beam_eval(_model(oracle, z_hit=1.0), z, np.full_like(z, zs))
+        np.testing.assert_allclose(p, stats.norm.pdf(z, loc=zs, scale=8.0), rtol=1e-12, atol=1e-300)
+        p, _ = oracle.beam_eval(_model(oracle, z_hit=1.0, hit_truncnorm=1), z, np.full_like(z, zs))
+        assert abs(integrate.trapezoid(p, z) - 1.0) < 1e-6
+        if zs > 0:
+            zz = np.linspace(0, zs, 20001)
+            p, _ = oracle.beam_eval(_model(oracle, z_short=1.0), zz, np.full_like(zz, zs))
+            assert abs(integrate.trapezoid(p, zz) - 1.0) < 1e-6
+            p, _ = oracle.beam_eval(_model(oracle, z_short=1.0), np.array([zs + 0.1]), np.array([zs]))
+            assert p[0] == 0.0
+    p, _ = oracle.beam_eval(_model(oracle, z_rand=1.0), z[:-1], np.full(z.size - 1, 10.0))
+    assert abs(integrate.trapezoid(p, z[:-1]) - 1.0) < 1e-3
+    p, _ = oracle.beam_eval(_model(oracle, z_max=1.0), np.array([mr, mr + 5, mr - 1e-3, 0.0]), np.full(4, 10.0))
+    np.testing.assert_array_equal(p, [1.0, 1.0, 0.0, 0.0])
+    # the mixture is linear in the weights
+    full = oracle.beam_model(mr)
+    zz = np.linspace(0, mr, 777)
+    zs = np.full_like(zz, 37.0)
+    parts = [oracle.beam_eval(_model(oracle, **{k: 1.0}), zz, zs)[0]
+             for k in ("z_hit", "z_short", "z_max", "z_rand")]
+    want = 0.75 * parts[0] + 0.01 * parts[1] + 0.07 * parts[2] + 0.12 * parts[3]
+    np.testing.assert_allclose(oracle.beam_eval(full, zz, zs)[0], want, rtol=1e-6)
+    assert abs((0.75 + 0.01 + 0.07 + 0.12) - 0.95) < 1e-12
+
+
+@pytest.mark.parametrize("trunc", [0, 1])
+def test_beam_model_derivative(oracle, trunc):
+    """The analytic dp/dz* equals a central difference of p in z*."""
+    m = oracle.beam_model(300.0, hit_truncnorm=trunc)
+    rs = synth.Stream(111)
+    zs = rs.uniform(4000, 0.5, 299.0)
+    z = rs.uniform(4000, 0.0, 300.0)
+    keep = np.abs(z - zs) > 1e-2
+    zs, z = zs[keep], z[keep]
+    h = 1e-5
+    p1, _ = oracle.beam_eval(m, z, zs + h)
+    p0, _ = oracle.beam_eval(m, z, zs - h)
+    _, dp = oracle.beam_eval(m, z, zs)
+    fd = (p1 - p0) / (2 * h)
+    np.testing.assert_allclose(dp, fd, rtol=1e-5, atol=1e-12)
+
+
+def test_logw_is_sum_of_log_beams(oracle):
+    """log w of a particle is the sum over its beams of log p(z_i | z*_i)."""
+    g = synth.rect_map(96, 96, n_rects=15, seed=121)
+    d = oracle.OracleCDDT(g, 108, 300.0)
+    bo = synth.beam_offsets(61)
+    parts = synth.uniform_particles(g, 50, seed=122)
+    obs = np.clip(synth.Stream(123).uniform(61, 0.0, 320.0), 0, 300).astype(np.float32)
+    m = oracle.beam_model(300.0)
+    logw, ranges = d.sensor_weights(parts, bo, obs, m, want_ranges=True)
+    for p in range(parts.shape[0]):
+        pv, _ = oracle.beam_eval(m, obs.astype(np.float64), ranges[p].astype(np.float64))
+        assert abs(np.sum(np.log(pv)) - logw[p]) < 1e-9 * max(1.0, abs(logw[p]))
+        q = np.stack([np.full(61, parts[p, 0]), np.full(61, parts[p, 1]),
+                      (parts[p, 2] + bo).astype(np.float32)], 1)
+        np.testing.assert_array_equal(d.calc_range(q), ranges[p])
+
+
+# ------------------------------------------------------------------ gradient
+
+def test_gradient_matches_finite_differences(oracle):
+    """d log w / d(x, y): the analytic float64 gradient equals a central finite
+    difference (delta = 1e-3 cell) of the float64 piecewise-linear log-weight,
+    within 1e-3 relative.  Per particle, a sample counts when no discrete
+    choice (cell, slice, bin, zero point, clamp, short-range indicator)
+    changes inside the stencil and no expected range lies in (0, 0.1) cell,
+    where the short-range density ~ 1/z* curves too fast for delta = 1e-3;
+    per beam, additionally when the beam's query point lies at least 0.25 cell
+    from a bin edge."""
+    g = synth.rect_map(128, 128, n_rects=20, seed=131)
+    N, mr = 108, 300.0
+    d = oracle.OracleCDDT(g, N, mr)
+    bo = synth.beam_offsets(61)
+    m = oracle.beam_model(mr)
+    gt = synth.uniform_particles(g, 1, seed=132)[0]
+    q = np.stack([np.full(61, gt[0]), np.full(61, gt[1]), (gt[2] + bo).astype(np.float32)], 1)
+    obs = np.clip(d.calc_range(q) + synth.noise(61, 2.0, seed=133), 0, mr).astype(np.float32)
+    parts = synth.tracking_particles(gt.astype(np.float64), 300, seed=134)
+    grad_main, _ = d.sensor_grad(parts, bo, obs, m)
+    delta = 1e-3
+    p = d.params
+
+    def fd_check(x, y, th, bo_, obs_):
+        qq = np.stack([np.full(bo_.size, x), np.full(bo_.size, y), (np.float32(th) + bo_)], 1)
+        zs = d.calc_range(qq)
+        if np.any((zs > 0) & (zs < 0.1)):
+            return None
+        v0, s0, g0 = d.logw_piecewise(x, y, th, bo_, obs_, m)
+        vals = []
+        for dx, dy in ((delta, 0), (-delta, 0), (0, delta), (0, -delta)):
+            v, s_, _ = d.logw_piecewise(x + dx, y + dy, th, bo_, obs_, m)
+            if s_ != s0:
+                return None
+            vals.append(v)
+        fd = np.array([(vals[0] - vals[1]) / (2 * delta), (vals[2] - vals[3]) / (2 * delta)])
+        return fd, g0
+
+    n_part = n_beam = nonzero = 0
+    for t in range(parts.shape[0]):
+        x, y, th = float(parts[t, 0]), float(parts[t, 1]), parts[t, 2]
+        r = fd_check(x, y, th, bo, obs)
+        if r is not None:
+            fd, g0 = r
+            scale = max(np.linalg.norm(g0), 1e-9)
+            assert np.linalg.norm(fd - g0) <= 1e-3 * scale + 1e-9, (t, fd, g0)
+            # the oracle's gradient on float32 ranges agrees with it
+            assert np.linalg.norm(grad_main[t] - g0) <= 1e-3 * scale + 1e-9
+            n_part += 1
+            nonzero += np.linalg.norm(g0) > 0
+        ths = (np.float32(th) + bo).astype(np.float32)
+        ks = np.array([p.query_k(a) for a in ths]) % (N // 2)
+        yr = np.float32(y) * p.c[ks] - np.float32(x) * p.s[ks]
+        for i in np.flatnonzero(np.abs((yr % 1.0) - 0.5) >= 0.25)[:6]:
+            r = fd_check(x, y, th, bo[i:i + 1], obs[i:i + 1])
+            if r is None:
+                continue
+            fd, g0 = r
+            scale = max(np.linalg.norm(g0), 1e-9)
+            assert np.linalg.norm(fd - g0) <= 1e-3 * scale + 1e-9, (t, i, fd, g0)
+            n_beam += 1
+    assert n_part > 100 and nonzero > 50 and n_beam > 500
