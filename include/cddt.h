@@ -1,0 +1,277 @@
+/*
+ * cddt.h -- C ABI of the GB300 CDDT library (libcddt.so).
+ *
+ * Compressed Directional Distance Transform ray casting fused with the beam
+ * sensor model of Monte Carlo localization (Walsh & Karaman, arXiv
+ * 1705.01167).  Section citations below refer to that paper.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers whose name ends in _dev are device memory owned by the caller
+ *    (for example torch tensors); the library never frees them.  Pointers
+ *    ending in _host are host memory owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Calls that launch work are stream-ordered and return
+ *    before it finishes unless stated otherwise.
+ *  - A handle (cddt_t) owns all device memory of one CDDT: the zero-point
+ *    store, the slice tables and a private copy of the occupancy grid (the
+ *    update writes it).  A handle is bound to the device that was current
+ *    when it was built; every call on it must run with that device current.
+ *    A handle is not thread-safe: serialise calls on one handle.
+ *  - Every call returns a cddt_status and never aborts the process.
+ *    Argument errors are detected on the host before any launch.  A kernel
+ *    that detects bad input (for example an out-of-map cell in an update)
+ *    records CDDT_ERR_DEVICE in the handle's device status word and skips
+ *    that item; cddt_get_status() reports and clears it.
+ *  - Coordinates are in cells.  Cell (i, j) is grid[j*W + i], centred on
+ *    the integer point (i, j); theta is in radians from +x toward +y.
+ *  - The CUDA extension does no work on the CPU: without a CUDA device
+ *    every call returns CDDT_ERR_CUDA.
+ */
+#ifndef CDDT_H
+#define CDDT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CDDT_API __attribute__((visibility("default")))
+#else
+#define CDDT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cddt_s *cddt_t;
+
+typedef enum {
+    CDDT_OK = 0,
+    CDDT_ERR_ARG = 1,     /* invalid argument (detected on the host)               */
+    CDDT_ERR_CUDA = 2,    /* a CUDA runtime call failed, or no CUDA device          */
+    CDDT_ERR_OOM = 3,     /* device allocation failed                               */
+    CDDT_ERR_PRUNED = 4,  /* incremental update of a pruned CDDT (Section IV-D)     */
+    CDDT_ERR_TIMEOUT = 5, /* a bounded device-side wait gave up                     */
+    CDDT_ERR_DEVICE = 6   /* a kernel flagged bad input; see cddt_get_status        */
+} cddt_status;
+
+/* Build flags. */
+#define CDDT_ZP_U16 1u /* 16-bit zero points (Section IV-C, "16 bit integers")     */
+
+/* Search layouts for queries (cddt_set_search).  Both give identical answers. */
+#define CDDT_SEARCH_TREE 0   /* implicit 8-ary max-separator tree over each bin     */
+#define CDDT_SEARCH_BINARY 1 /* branch-free binary search of the sorted bin          */
+
+/* Beam sensor model (Section VI, "beam mode sensor model"; the mixture of the
+ * textbook beam model).  p(z | z*) = z_hit p_hit + z_short p_short + z_max
+ * p_max + z_rand p_rand with
+ *   p_hit   = N(z; z*, sigma_hit^2), optionally divided by its mass on
+ *             [0, max_range] when hit_truncnorm != 0
+ *   p_short = lambda e^{-lambda z} / (1 - e^{-lambda z*}) for 0 <= z <= z*,
+ *             z* > 0; else 0
+ *   p_max   = 1 if z >= max_range else 0
+ *   p_rand  = 1/max_range if z < max_range else 0
+ * where z is the measured range clamped to [0, max_range] and z* the CDDT
+ * range.  The weights are used as given (not renormalised). */
+typedef struct {
+    float z_hit, z_short, z_max, z_rand;
+    float sigma_hit;
+    float lambda_short;
+    float max_range;
+    int32_t hit_truncnorm;
+} cddt_beam_model;
+
+typedef struct {
+    int32_t W, H, theta_disc, n_slices; /* n_slices = theta_disc / 2 stored slices   */
+    float max_range;
+    uint32_t flags;
+    int32_t pruned;
+    int64_t total_bins;
+    int64_t n_zero_points;   /* zero points stored (after pruning / updates)      */
+    int64_t n_edge_cells;    /* edge cells at build time                          */
+    int64_t store_bytes;     /* bytes of the zero-point store incl. tree nodes    */
+    int64_t max_bin;         /* largest bin                                       */
+    float build_ms, prune_ms, update_ms; /* device time of the last such call     */
+} cddt_stats;
+
+/* Build a CDDT from an occupancy grid (Section IV-A, direct construction).
+ *   grid_dev    uint8 [H][W], nonzero = occupied; read during the call only.
+ *   W, H        1 .. 32767.
+ *   theta_disc  N >= 2, even: directions 2 pi k / N over the full circle;
+ *               N/2 slices are stored (Section IV-C symmetry).
+ *   max_range   > 0, in cells; ranges are clamped to it.
+ *   flags       0 or CDDT_ZP_U16.
+ *   out         receives the handle.
+ * Synchronises `stream` (allocation sizes depend on the zero-point count).
+ * Errors: ARG, CUDA, OOM. */
+CDDT_API cddt_status cddt_build(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t theta_disc,
+                       float max_range, uint32_t flags, void *stream, cddt_t *out);
+
+/* Free every device buffer of the handle (synchronises the device first).
+ * NULL is accepted. */
+CDDT_API cddt_status cddt_destroy(cddt_t h);
+
+/* Prune (Section IV-C, PCDDT): remove every zero point that no query from a
+ * free cell can return; answers of such queries do not change.  A pruned
+ * handle rejects cddt_update_cells (Section IV-D).  Synchronises `stream`.
+ * Errors: ARG, CUDA, OOM, PRUNED (already pruned). */
+CDDT_API cddt_status cddt_prune(cddt_t h, void *stream);
+
+/* Incremental update (Section IV-D): apply n cell writes in order, later
+ * writes to the same cell winning.  xy_dev int32 [n][2] = (x, y) cells,
+ * occ_dev uint8 [n] (nonzero = occupied).  Afterwards the zero points equal
+ * those of cddt_build on the updated grid, including obstacles revealed or
+ * hidden by the edge-map erosion.  Writes outside the map are skipped and
+ * flag CDDT_ERR_DEVICE.  May synchronise `stream` when the store must grow.
+ * Errors: ARG, CUDA, OOM, PRUNED. */
+CDDT_API cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const uint8_t *occ_dev, int32_t n,
+                              void *stream);
+
+/* Ray casting (Section IV-B query, Section IV-C reverse search): n queries
+ * pose_dev float [n][3] = (x, y, theta) -> range_dev float [n].  A query whose
+ * nearest cell is occupied or off the map returns 0; a ray that meets no
+ * zero point returns max_range.  sort_by_slice != 0 first orders the queries
+ * by slice (a counting sort on the device) so that the gathers of one slice
+ * run together; the answers are the same.  scratch: with sort_by_slice the
+ * handle keeps an internal scratch of 8 bytes per query (grown on demand;
+ * growing synchronises `stream`).  Errors: ARG, CUDA, OOM. */
+CDDT_API cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
+                                 int32_t sort_by_slice, void *stream);
+
+/* Fused sensor model (Section VI): for every particle p, log w_p =
+ * sum_i log p(obs_i | z*_i), z*_i the CDDT range from (x_p, y_p) at theta_p +
+ * beam_off_i (one float32 add).
+ *   particles_dev float [P][3]; beam_off_dev, obs_dev float [B] (shared by all
+ *   particles); logw_dev float [P]; ranges_dev float [P][B] or NULL.
+ *   pair_offset D: 0, or the index distance between opposite beams
+ *   (beam_off[i + D] - beam_off[i] = pi, B/2 <= D < B).  Paired beams whose
+ *   directions fall on the same stored slice share one search (Section IV-C);
+ *   D only affects speed, never the result.
+ * Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_sensor_weights(cddt_t h, const float *particles_dev, int64_t P,
+                                const float *beam_off_dev, const float *obs_dev, int32_t B,
+                                int32_t pair_offset, const cddt_beam_model *m, float *logw_dev,
+                                float *ranges_dev, void *stream);
+
+/* Adjoint of cddt_sensor_weights: grad_xy_dev float [P][2] = grad_logw_p *
+ * d log w_p / d(x_p, y_p).  The range is linear in the rotated abscissa
+ * x' = x cos(theta_k) + y sin(theta_k) (Section IV-B), so the derivative of
+ * z* by (x, y) is -(cos, sin) of the discrete direction (+ for the reverse
+ * search); it is 0
+ * for a clamped range, a miss, and a particle in an occupied or off-map
+ * cell.  The derivative in theta is 0 almost everywhere (theta is rounded to
+ * a slice) and is not returned.  Recomputes the searches.
+ * Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_sensor_weights_backward(cddt_t h, const float *particles_dev, int64_t P,
+                                         const float *beam_off_dev, const float *obs_dev,
+                                         int32_t B, int32_t pair_offset, const cddt_beam_model *m,
+                                         const float *grad_logw_dev, float *grad_xy_dev,
+                                         void *stream);
+
+/* Forward and adjoint in one pass: logw_dev [P] and grad_xy_dev [P][2] with
+ * grad_logw = 1.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_sensor_weights_fwd_bwd(cddt_t h, const float *particles_dev, int64_t P,
+                                        const float *beam_off_dev, const float *obs_dev,
+                                        int32_t B, int32_t pair_offset, const cddt_beam_model *m,
+                                        float *logw_dev, float *grad_xy_dev, void *stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/* One filter of a batch: its CDDT, particles, scan and model.  Several
+ * filters may share a handle (for example successive filter steps on one
+ * map).  All pointers are device memory owned by the caller and must stay
+ * valid while the plan is used. */
+typedef struct {
+    cddt_t map;
+    const float *particles_dev; /* [P][3] */
+    int64_t P;
+    const float *beam_off_dev; /* [B] */
+    const float *obs_dev;      /* [B] */
+    int32_t B;
+    int32_t pair_offset;
+    cddt_beam_model model;
+    float *logw_dev; /* [P] */
+} cddt_filter;
+
+typedef struct cddt_plan_s *cddt_plan;
+
+/* Make a plan that weights many filters (maps of any size, any theta_disc,
+ * any particle count) in one persistent launch.  Blocks take work items
+ * (filter, particle range) from a device work queue.  The work table is
+ * uploaded here; the plan keeps its own copy of the filter descriptors.
+ * Synchronises `stream`.  Errors: ARG, CUDA, OOM. */
+CDDT_API cddt_status cddt_plan_create(const cddt_filter *filters_host, int32_t n_filters, void *stream,
+                             cddt_plan *out);
+
+/* Pick block size, threads per particle and particles per work item by
+ * timing candidate launches on `stream` (the plan's filters are evaluated
+ * several times; outputs are overwritten).  Synchronises `stream`.
+ * Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_plan_autotune(cddt_plan p, void *stream);
+
+/* Set the launch shape by hand: tpp in {1,2,4,8,16,32} threads per particle,
+ * ppi particles per work item (multiple of 32 / tpp), block threads in
+ * {64..1024} multiple of 32.  Errors: ARG. */
+CDDT_API cddt_status cddt_plan_set_shape(cddt_plan p, int32_t tpp, int32_t ppi, int32_t block);
+CDDT_API cddt_status cddt_plan_get_shape(cddt_plan p, int32_t *tpp, int32_t *ppi, int32_t *block);
+
+/* Run the plan on `stream`: reset the queue and launch once.  Safe to
+ * capture in a CUDA graph.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_plan_run(cddt_plan p, void *stream);
+
+/* Capture cddt_plan_run into a CUDA graph owned by the plan and launch that
+ * graph on later calls of cddt_plan_launch_graph.  The capture happens on
+ * the first call.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_plan_launch_graph(cddt_plan p, void *stream);
+
+/* Number of work items of the plan, and of filters. */
+CDDT_API int64_t cddt_plan_items(cddt_plan p);
+
+CDDT_API cddt_status cddt_plan_destroy(cddt_plan p);
+
+/* ---------------------------------------------------------------- support */
+
+/* Choose the search layout used by later queries (CDDT_SEARCH_*). */
+CDDT_API cddt_status cddt_set_search(cddt_t h, int32_t search);
+
+/* Size and timing figures of a handle.  Synchronises the device. */
+CDDT_API cddt_status cddt_get_stats(cddt_t h, cddt_stats *out);
+
+/* Synchronise the device and return the handle's device status word
+ * (CDDT_OK, CDDT_ERR_DEVICE or CDDT_ERR_TIMEOUT), clearing it. */
+CDDT_API cddt_status cddt_get_status(cddt_t h);
+
+/* Copy the CDDT to host memory in plain CSR form, for checks and
+ * checkpointing: slice_base_host int64 [n_slices + 1] (first global bin of
+ * each slice), bin_start_host int64 [total_bins + 1], zp_host float
+ * [n_zero_points] (for CDDT_ZP_U16 the dequantised values), each bin sorted
+ * ascending.  Any pointer may be NULL to skip it.  Synchronises the device.
+ * Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_export(cddt_t h, int64_t *slice_base_host, int64_t *bin_start_host,
+                        float *zp_host);
+
+/* Copy the handle's occupancy grid and edge map (uint8 [H][W]) to the host.
+ * Either pointer may be NULL.  Synchronises the device.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_export_grid(cddt_t h, uint8_t *grid_host, uint8_t *edge_host);
+
+/* Per-launch work figures of a cddt_sensor_weights call with the same
+ * arguments, for roofline accounting (no ranges or weights are produced):
+ *   out_host int64 [6] = { traversals, beams cast, searches with a
+ *   non-empty bin, sum over searches of ceil(log2(k_b + 1)) for bin size
+ *   k_b, paired reverse beams, particles passing the occupancy check }.
+ * Synchronises `stream`.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_sensor_work(cddt_t h, const float *particles_dev, int64_t P,
+                             const float *beam_off_dev, int32_t B, int32_t pair_offset,
+                             int64_t *out_host, void *stream);
+
+/* A short message for a status code (static storage). */
+CDDT_API const char *cddt_status_string(cddt_status s);
+
+/* Library version, for checks that the right build is loaded. */
+CDDT_API int32_t cddt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDDT_H */

@@ -1,0 +1,413 @@
+"""Thin Python binding of libcddt.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module checks
+tensor shapes, dtypes and devices, passes raw device pointers and the current
+torch CUDA stream, and turns status codes into exceptions.  There is no CPU
+path: without the built library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+CDDT_OK, CDDT_ERR_ARG, CDDT_ERR_CUDA, CDDT_ERR_OOM, CDDT_ERR_PRUNED, CDDT_ERR_TIMEOUT, CDDT_ERR_DEVICE = range(7)
+CDDT_ZP_U16 = 1
+SEARCH_TREE, SEARCH_BINARY = 0, 1
+
+EXPORTED = (
+    "cddt_build", "cddt_destroy", "cddt_prune", "cddt_update_cells", "cddt_calc_range_many",
+    "cddt_sensor_weights", "cddt_sensor_weights_backward", "cddt_sensor_weights_fwd_bwd",
+    "cddt_plan_create", "cddt_plan_autotune", "cddt_plan_set_shape", "cddt_plan_get_shape",
+    "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
+    "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
+    "cddt_sensor_work", "cddt_status_string", "cddt_version",
+)
+
+
+class CDDTError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class BeamModel(C.Structure):
+    """cddt_beam_model: the beam sensor model mixture (Section VI)."""
+    _fields_ = [("z_hit", C.c_float), ("z_short", C.c_float), ("z_max", C.c_float),
+                ("z_rand", C.c_float), ("sigma_hit", C.c_float), ("lambda_short", C.c_float),
+                ("max_range", C.c_float), ("hit_truncnorm", C.c_int32)]
+
+
+def beam_model(max_range: float, z_hit=0.75, z_short=0.01, z_max=0.07, z_rand=0.12,
+               sigma_hit=8.0, lambda_short=0.01, hit_truncnorm=0) -> BeamModel:
+    return BeamModel(z_hit, z_short, z_max, z_rand, sigma_hit, lambda_short, max_range,
+                     int(hit_truncnorm))
+
+
+class Stats(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("theta_disc", C.c_int32),
+                ("n_slices", C.c_int32), ("max_range", C.c_float), ("flags", C.c_uint32),
+                ("pruned", C.c_int32), ("total_bins", C.c_int64), ("n_zero_points", C.c_int64),
+                ("n_edge_cells", C.c_int64), ("store_bytes", C.c_int64), ("max_bin", C.c_int64),
+                ("build_ms", C.c_float), ("prune_ms", C.c_float), ("update_ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Filter(C.Structure):
+    _fields_ = [("map", C.c_void_p), ("particles_dev", C.c_void_p), ("P", C.c_int64),
+                ("beam_off_dev", C.c_void_p), ("obs_dev", C.c_void_p), ("B", C.c_int32),
+                ("pair_offset", C.c_int32), ("model", BeamModel), ("logw_dev", C.c_void_p)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcddt.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcddt.so is not built ({path}); run paper_1705_01167_gb300.build")
+        L = C.CDLL(path)
+        vp, i32, i64, u32, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_float
+        st = C.c_int
+        sig = {
+            "cddt_build": (st, [vp, i32, i32, i32, f32, u32, vp, C.POINTER(vp)]),
+            "cddt_destroy": (st, [vp]),
+            "cddt_prune": (st, [vp, vp]),
+            "cddt_update_cells": (st, [vp, vp, vp, i32, vp]),
+            "cddt_calc_range_many": (st, [vp, vp, vp, i64, i32, vp]),
+            "cddt_sensor_weights": (st, [vp, vp, i64, vp, vp, i32, i32, C.POINTER(BeamModel), vp, vp, vp]),
+            "cddt_sensor_weights_backward": (st, [vp, vp, i64, vp, vp, i32, i32, C.POINTER(BeamModel), vp, vp, vp]),
+            "cddt_sensor_weights_fwd_bwd": (st, [vp, vp, i64, vp, vp, i32, i32, C.POINTER(BeamModel), vp, vp, vp]),
+            "cddt_plan_create": (st, [C.POINTER(Filter), i32, vp, C.POINTER(vp)]),
+            "cddt_plan_autotune": (st, [vp, vp]),
+            "cddt_plan_set_shape": (st, [vp, i32, i32, i32]),
+            "cddt_plan_get_shape": (st, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+            "cddt_plan_run": (st, [vp, vp]),
+            "cddt_plan_launch_graph": (st, [vp, vp]),
+            "cddt_plan_items": (i64, [vp]),
+            "cddt_plan_destroy": (st, [vp]),
+            "cddt_set_search": (st, [vp, i32]),
+            "cddt_get_stats": (st, [vp, C.POINTER(Stats)]),
+            "cddt_get_status": (st, [vp]),
+            "cddt_export": (st, [vp, vp, vp, vp]),
+            "cddt_export_grid": (st, [vp, vp, vp]),
+            "cddt_sensor_work": (st, [vp, vp, i64, vp, i32, i32, vp, vp]),
+            "cddt_status_string": (C.c_char_p, [st]),
+            "cddt_version": (i32, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def status_string(s: int) -> str:
+    return load().cddt_status_string(s).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != CDDT_OK:
+        raise CDDTError(rc, what)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype, name: str, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None:
+        for i, s in enumerate(shape):
+            if s is not None and t.shape[i] != s:
+                raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {shape}")
+    return t
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def pair_offset(beam_off) -> int:
+    """Index distance D with beam_off[i + D] - beam_off[i] = pi for every
+    paired i (0 when the layout has none).  Host-side hint only: the kernels
+    verify every pair and the result never depends on D."""
+    import numpy as np
+    b = np.asarray(beam_off.detach().cpu() if isinstance(beam_off, torch.Tensor) else beam_off,
+                   dtype=np.float64)
+    B = b.size
+    for D in range((B + 1) // 2, B):
+        d = b[D:] - b[:B - D]
+        if np.all(np.abs(d - math.pi) < 1e-5):
+            return D
+    return 0
+
+
+class CDDT:
+    """One Compressed Directional Distance Transform on the current CUDA
+    device (Section IV): ``cddt_build`` on a uint8 occupancy grid [H, W]."""
+
+    def __init__(self, grid: torch.Tensor, theta_disc: int, max_range: float, u16: bool = False,
+                 stream=None):
+        L = load()
+        _dev(grid, torch.uint8, "grid")
+        if grid.dim() != 2:
+            raise ValueError("grid must be [H, W]")
+        self.H, self.W = grid.shape
+        self.theta_disc = int(theta_disc)
+        self.max_range = float(max_range)
+        self.u16 = bool(u16)
+        self.device = grid.device
+        h = C.c_void_p()
+        with torch.cuda.device(grid.device):
+            rc = L.cddt_build(_ptr(grid), self.W, self.H, self.theta_disc, self.max_range,
+                              CDDT_ZP_U16 if u16 else 0, _stream(stream), C.byref(h))
+        _check(rc, "cddt_build")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cddt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- maintenance
+    def prune(self, stream=None):
+        with torch.cuda.device(self.device):
+            _check(load().cddt_prune(self._h, _stream(stream)), "cddt_prune")
+
+    def update_cells(self, xy: torch.Tensor, occ: torch.Tensor, stream=None):
+        _dev(xy, torch.int32, "xy")
+        _dev(occ, torch.uint8, "occ")
+        n = occ.numel()
+        if xy.numel() != 2 * n:
+            raise ValueError("xy must be [n, 2] and occ [n]")
+        with torch.cuda.device(self.device):
+            _check(load().cddt_update_cells(self._h, _ptr(xy), _ptr(occ), n, _stream(stream)),
+                   "cddt_update_cells")
+
+    def set_search(self, search: int):
+        _check(load().cddt_set_search(self._h, search), "cddt_set_search")
+
+    def stats(self) -> dict:
+        s = Stats()
+        with torch.cuda.device(self.device):
+            _check(load().cddt_get_stats(self._h, C.byref(s)), "cddt_get_stats")
+        return s.as_dict()
+
+    def status(self) -> int:
+        with torch.cuda.device(self.device):
+            return load().cddt_get_status(self._h)
+
+    def export(self):
+        """(slice_base int64 [S+1], bin_start int64 [bins+1], zp float32 [n]) on the host."""
+        import numpy as np
+        st = self.stats()
+        sb = np.empty(st["n_slices"] + 1, np.int64)
+        bs = np.empty(st["total_bins"] + 1, np.int64)
+        zp = np.empty(max(st["n_zero_points"], 1), np.float32)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_export(self._h, sb.ctypes.data_as(C.c_void_p),
+                                      bs.ctypes.data_as(C.c_void_p),
+                                      zp.ctypes.data_as(C.c_void_p)), "cddt_export")
+        return sb, bs, zp[:bs[-1]].copy()
+
+    def export_grid(self):
+        import numpy as np
+        g = np.empty((self.H, self.W), np.uint8)
+        e = np.empty((self.H, self.W), np.uint8)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_export_grid(self._h, g.ctypes.data_as(C.c_void_p),
+                                           e.ctypes.data_as(C.c_void_p)), "cddt_export_grid")
+        return g, e
+
+    # ---- queries
+    def calc_range_many(self, poses: torch.Tensor, sort_by_slice: bool = False,
+                        out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        _dev(poses, torch.float32, "poses")
+        n = poses.numel() // 3
+        if poses.numel() != 3 * n:
+            raise ValueError("poses must be [n, 3]")
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=poses.device)
+        _dev(out, torch.float32, "out")
+        with torch.cuda.device(self.device):
+            _check(load().cddt_calc_range_many(self._h, _ptr(poses), _ptr(out), n,
+                                               int(bool(sort_by_slice)), _stream(stream)),
+                   "cddt_calc_range_many")
+        return out
+
+    def _sensor_args(self, particles, beam_off, obs):
+        _dev(particles, torch.float32, "particles")
+        _dev(beam_off, torch.float32, "beam_off")
+        _dev(obs, torch.float32, "obs")
+        P = particles.numel() // 3
+        B = beam_off.numel()
+        if particles.numel() != 3 * P or obs.numel() != B:
+            raise ValueError("particles must be [P, 3] and obs [B] like beam_off")
+        return P, B
+
+    def sensor_weights(self, particles, beam_off, obs, model: BeamModel, pair_offset: int = 0,
+                       want_ranges: bool = False, logw=None, stream=None):
+        P, B = self._sensor_args(particles, beam_off, obs)
+        if logw is None:
+            logw = torch.empty(P, dtype=torch.float32, device=particles.device)
+        ranges = torch.empty((P, B), dtype=torch.float32, device=particles.device) if want_ranges else None
+        with torch.cuda.device(self.device):
+            _check(load().cddt_sensor_weights(self._h, _ptr(particles), P, _ptr(beam_off), _ptr(obs),
+                                              B, pair_offset, C.byref(model), _ptr(logw),
+                                              _ptr(ranges), _stream(stream)),
+                   "cddt_sensor_weights")
+        return (logw, ranges) if want_ranges else logw
+
+    def sensor_weights_backward(self, particles, beam_off, obs, model: BeamModel, grad_logw,
+                                pair_offset: int = 0, grad_xy=None, stream=None):
+        P, B = self._sensor_args(particles, beam_off, obs)
+        _dev(grad_logw, torch.float32, "grad_logw")
+        if grad_xy is None:
+            grad_xy = torch.empty((P, 2), dtype=torch.float32, device=particles.device)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_sensor_weights_backward(self._h, _ptr(particles), P, _ptr(beam_off),
+                                                       _ptr(obs), B, pair_offset, C.byref(model),
+                                                       _ptr(grad_logw), _ptr(grad_xy),
+                                                       _stream(stream)),
+                   "cddt_sensor_weights_backward")
+        return grad_xy
+
+    def sensor_weights_fwd_bwd(self, particles, beam_off, obs, model: BeamModel,
+                               pair_offset: int = 0, logw=None, grad_xy=None, stream=None):
+        P, B = self._sensor_args(particles, beam_off, obs)
+        if logw is None:
+            logw = torch.empty(P, dtype=torch.float32, device=particles.device)
+        if grad_xy is None:
+            grad_xy = torch.empty((P, 2), dtype=torch.float32, device=particles.device)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_sensor_weights_fwd_bwd(self._h, _ptr(particles), P, _ptr(beam_off),
+                                                      _ptr(obs), B, pair_offset, C.byref(model),
+                                                      _ptr(logw), _ptr(grad_xy), _stream(stream)),
+                   "cddt_sensor_weights_fwd_bwd")
+        return logw, grad_xy
+
+    def sensor_work(self, particles, beam_off, pair_offset: int = 0, stream=None):
+        """Work figures of one sensor_weights launch (see cddt.h)."""
+        import numpy as np
+        _dev(particles, torch.float32, "particles")
+        _dev(beam_off, torch.float32, "beam_off")
+        out = np.zeros(6, np.int64)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_sensor_work(self._h, _ptr(particles), particles.numel() // 3,
+                                           _ptr(beam_off), beam_off.numel(), pair_offset,
+                                           out.ctypes.data_as(C.c_void_p), _stream(stream)),
+                   "cddt_sensor_work")
+        keys = ("traversals", "beams", "nonempty", "probes", "paired", "passed")
+        return dict(zip(keys, (int(v) for v in out)))
+
+
+class SensorWeights(torch.autograd.Function):
+    """log w = cddt_sensor_weights(particles); backward = the adjoint kernel
+    (d log w / d(x, y); the theta column receives zero gradient)."""
+
+    @staticmethod
+    def forward(ctx, particles, cddt: CDDT, beam_off, obs, model: BeamModel, pair_offset: int = 0):
+        p = particles.detach().contiguous()
+        logw = cddt.sensor_weights(p, beam_off, obs, model, pair_offset)
+        ctx.save_for_backward(p)
+        ctx.cddt, ctx.beam_off, ctx.obs, ctx.model, ctx.D = cddt, beam_off, obs, model, pair_offset
+        return logw
+
+    @staticmethod
+    def backward(ctx, grad_logw):
+        (p,) = ctx.saved_tensors
+        g = ctx.cddt.sensor_weights_backward(p, ctx.beam_off, ctx.obs, ctx.model,
+                                             grad_logw.contiguous().float(), ctx.D)
+        grad = torch.zeros_like(p)
+        grad[:, :2] = g
+        return grad, None, None, None, None, None
+
+
+class Plan:
+    """Many filters (maps of any size, any particle count) weighted in one
+    persistent launch (``cddt_plan_*``), optionally replayed as a CUDA graph."""
+
+    def __init__(self, filters: list[dict], stream=None):
+        L = load()
+        arr = (Filter * len(filters))()
+        self._keep = []
+        for i, f in enumerate(filters):
+            m: CDDT = f["map"]
+            P, B = m._sensor_args(f["particles"], f["beam_off"], f["obs"])
+            _dev(f["logw"], torch.float32, "logw")
+            arr[i] = Filter(m.handle.value, f["particles"].data_ptr(), P, f["beam_off"].data_ptr(),
+                            f["obs"].data_ptr(), B, int(f.get("pair_offset", 0)), f["model"],
+                            f["logw"].data_ptr())
+            self._keep.append(f)
+        h = C.c_void_p()
+        _check(L.cddt_plan_create(arr, len(filters), _stream(stream), C.byref(h)), "cddt_plan_create")
+        self._h = h
+
+    def autotune(self, stream=None):
+        _check(load().cddt_plan_autotune(self._h, _stream(stream)), "cddt_plan_autotune")
+        return self.shape()
+
+    def set_shape(self, tpp: int, ppi: int, block: int):
+        _check(load().cddt_plan_set_shape(self._h, tpp, ppi, block), "cddt_plan_set_shape")
+
+    def shape(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().cddt_plan_get_shape(self._h, C.byref(a), C.byref(b), C.byref(c)), "cddt_plan_get_shape")
+        return {"tpp": a.value, "ppi": b.value, "block": c.value}
+
+    def run(self, stream=None):
+        _check(load().cddt_plan_run(self._h, _stream(stream)), "cddt_plan_run")
+
+    def launch_graph(self, stream=None):
+        _check(load().cddt_plan_launch_graph(self._h, _stream(stream)), "cddt_plan_launch_graph")
+
+    @property
+    def items(self) -> int:
+        return load().cddt_plan_items(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cddt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

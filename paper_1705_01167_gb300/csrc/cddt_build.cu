@@ -1,0 +1,659 @@
+// cddt_build.cu -- GPU construction of the CDDT (Section IV-A), shared
+// scan / sort / index kernels (also used by prune and update).
+//
+// Construction, following the direct construction algorithm: the edge map
+// (occupied cells with a free or off-map 8-neighbour) is computed, every
+// (edge cell, slice) pair is projected into the slice and counted in each
+// bin its rotated square overlaps, the per-bin counts are laid out into
+// 32-byte aligned runs, the projected abscissae are scattered, each bin is
+// sorted (the sorted-vector successor structure of Section IV-B) and the
+// implicit search tree of every bin is filled from its sorted keys.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "cddt_internal.cuh"
+#include "cddt_kernels.cuh"
+
+namespace cddt {
+
+cddt_status cuda_status(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) return CDDT_ERR_OOM;
+    return CDDT_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ scan
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *warp_sums, uint64_t &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        uint64_t w = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    uint64_t before = wid ? warp_sums[wid - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void scan_reduce_kernel(const uint32_t *in, int64_t n, uint64_t *partial)
+{
+    __shared__ uint64_t ws[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    uint64_t tot;
+    block_exclusive_scan(s, ws, tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void scan_partials_kernel(uint64_t *partial, int64_t nblocks, uint64_t *total)
+{
+    __shared__ uint64_t ws[32];
+    uint64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+        int64_t i = b0 + threadIdx.x;
+        uint64_t v = i < nblocks ? partial[i] : 0;
+        uint64_t tot;
+        uint64_t ex = block_exclusive_scan(v, ws, tot);
+        if (i < nblocks) partial[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_apply_kernel(const uint32_t *in, int64_t n, const uint64_t *partial, uint32_t *out)
+{
+    __shared__ uint64_t ws[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint64_t v[kScanItems];
+    uint64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        s += v[i];
+    }
+    uint64_t tot;
+    uint64_t ex = block_exclusive_scan(s, ws, tot) + partial[blockIdx.x];
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = (uint32_t)ex;
+        ex += v[i];
+    }
+}
+
+// Exclusive scan of n uint32 values into out (may alias in); the total is
+// written to total_dev.  scratch: >= (n / kScanTile + 1) uint64.
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *scratch,
+                        uint64_t *total_dev, cudaStream_t st)
+{
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 0) {
+        cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), st);
+        return;
+    }
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, scratch);
+    scan_partials_kernel<<<1, 1024, 0, st>>>(scratch, nb, total_dev);
+    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, scratch, out);
+}
+
+int64_t scan_scratch_elems(int64_t n) { return n / kScanTile + 2; }
+
+// ------------------------------------------------------------ grid kernels
+
+__global__ void normalise_grid_kernel(const uint8_t *in, uint8_t *out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] ? 1 : 0;
+}
+
+// Edge map (Section IV-A: map minus its 3x3 erosion; off-map is free).
+__global__ void edge_map_kernel(const uint8_t *g, uint8_t *edge, int W, int H)
+{
+    int64_t n = (int64_t)W * H;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(q / W), i = (int)(q - (int64_t)j * W);
+        edge[q] = edge_at(g, W, H, i, j);
+    }
+}
+
+
+// Row-major compaction of nonzero flags into cell indices (deterministic).
+__global__ void flag_count_kernel(const uint8_t *flag, int64_t n, uint32_t *block_count)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int v = (i < n) && flag[i];
+    int c = __syncthreads_count(v);
+    if (threadIdx.x == 0) block_count[blockIdx.x] = (uint32_t)c;
+}
+
+__global__ void flag_write_kernel(const uint8_t *flag, int64_t n, const uint32_t *block_off, uint32_t *out)
+{
+    __shared__ uint32_t wcount[32];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int v = (i < n) && flag[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned m = __ballot_sync(0xffffffffu, v);
+    if (lane == 0) wcount[wid] = __popc(m);
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < wid; ++w) before += wcount[w];
+    if (v) out[block_off[blockIdx.x] + before + __popc(m & ((1u << lane) - 1))] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------ construction
+
+// Count: every (edge cell, slice) adds one to each bin it overlaps.
+__global__ void count_kernel(const uint32_t *cells, int64_t E, int W, const SliceInfo *slices, int S,
+                             uint32_t *count)
+{
+    int64_t total = E * S;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int s = (int)(t / E);
+        int64_t e = t - (int64_t)s * E;
+        uint32_t q = cells[e];
+        int j = (int)(q / (uint32_t)W), i = (int)(q - (uint32_t)j * W);
+        SliceInfo si = slices[s];
+        float xr, yr;
+        project((float)i, (float)j, si.c, si.s, xr, yr);
+        int b0, b1;
+        if (!cell_bins(yr, half_extent(si.c, si.s), si.T, si.nb, b0, b1)) continue;
+        for (int b = b0; b <= b1; ++b) atomicAdd(count + si.sbase + b, 1u);
+    }
+}
+
+template <int LK>
+__global__ void nodes_kernel(const uint32_t *count, int64_t nbins, uint32_t *nodes)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
+         g += (int64_t)gridDim.x * blockDim.x)
+        nodes[g] = bin_nodes(count[g], LK);
+}
+
+__global__ void bins_kernel(const uint32_t *count, const uint32_t *node_off, int64_t nbins, uint2 *bins,
+                            unsigned long long *max_bin)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        bins[g] = make_uint2(node_off[g], count[g]);
+        if (count[g]) atomicMax(max_bin, (unsigned long long)count[g]);
+    }
+}
+
+template <typename KT>
+__device__ __forceinline__ KT *leaf_run(void *store, uint2 bi)
+{
+    constexpr int LK = KeyT<KT>::LK;
+    return reinterpret_cast<KT *>(store) + ((size_t)(bi.x + internal_nodes(bi.y, LK)) << LK);
+}
+
+// Scatter: the projected abscissa of every (edge cell, slice, bin) into the
+// bin's leaf run, at a slot taken from a per-bin cursor (the order is fixed by
+// the sort that follows).
+template <typename KT>
+__global__ void scatter_kernel(const uint32_t *cells, int64_t E, int W, const SliceInfo *slices, int S,
+                               const uint2 *bins, uint32_t *cursor, void *store, float Q)
+{
+    int64_t total = E * S;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int s = (int)(t / E);
+        int64_t e = t - (int64_t)s * E;
+        uint32_t q = cells[e];
+        int j = (int)(q / (uint32_t)W), i = (int)(q - (uint32_t)j * W);
+        SliceInfo si = slices[s];
+        float xr, yr;
+        project((float)i, (float)j, si.c, si.s, xr, yr);
+        int b0, b1;
+        if (!cell_bins(yr, half_extent(si.c, si.s), si.T, si.nb, b0, b1)) continue;
+        for (int b = b0; b <= b1; ++b) {
+            uint32_t g = si.sbase + b;
+            uint2 bi = bins[g];
+            uint32_t pos = atomicAdd(cursor + g, 1u);
+            KT *run = leaf_run<KT>(store, bi);
+            if (sizeof(KT) == 4)
+                reinterpret_cast<float *>(run)[pos] = xr;
+            else
+                reinterpret_cast<uint16_t *>(run)[pos] = quantise(xr, si.X, Q);
+        }
+    }
+}
+
+// ------------------------------------------------------------ segmented sort
+
+template <typename KT> __device__ __forceinline__ KT pad_key();
+template <> __device__ __forceinline__ float pad_key<float>() { return kInf; }
+template <> __device__ __forceinline__ uint16_t pad_key<uint16_t>() { return 0xffffu; }
+
+// Size classes of the per-bin sort.
+constexpr uint32_t kWarpSortMax = 32;
+constexpr uint32_t kBlockSortMax = 2048;
+constexpr uint32_t kBigSortMax = 16384;
+
+__global__ void classify_kernel(const uint2 *bins, int64_t nbins, uint32_t *lists, uint32_t *list_n,
+                                int64_t cap)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t n = bins[g].y;
+        int cls;
+        if (n <= 1) continue;
+        if (n <= kWarpSortMax) cls = 0;
+        else if (n <= kBlockSortMax) cls = 1;
+        else if (n <= kBigSortMax) cls = 2;
+        else cls = 3;
+        uint32_t pos = atomicAdd(list_n + cls, 1u);
+        lists[cls * cap + pos] = (uint32_t)g;
+    }
+}
+
+__device__ __forceinline__ float shfl_xor_key(float v, int j) { return __shfl_xor_sync(0xffffffffu, v, j); }
+__device__ __forceinline__ uint16_t shfl_xor_key(uint16_t v, int j)
+{
+    return (uint16_t)__shfl_xor_sync(0xffffffffu, (uint32_t)v, j);
+}
+
+// Ascending bitonic sort of 32 keys held one per lane.
+template <typename KT>
+__device__ __forceinline__ KT warp_bitonic(KT v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            KT o = shfl_xor_key(v, j);
+            bool up = ((lane & k) == 0);
+            bool lower = ((lane & j) == 0);
+            KT mn = v < o ? v : o, mx = v < o ? o : v;
+            v = (lower == up) ? mn : mx;
+        }
+    }
+    return v;
+}
+
+template <typename KT>
+__global__ void warp_sort_kernel(void *store, const uint2 *bins, const uint32_t *list, uint32_t count)
+{
+    const int lane = threadIdx.x & 31;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count;
+         w += (gridDim.x * blockDim.x) >> 5) {
+        uint2 bi = bins[list[w]];
+        KT *run = leaf_run<KT>(store, bi);
+        KT v = lane < (int)bi.y ? run[lane] : pad_key<KT>();
+        v = warp_bitonic<KT>(v);
+        if (lane < (int)bi.y) run[lane] = v;
+    }
+}
+
+// Block bitonic sort in shared memory, padded to a power of two with +inf.
+template <typename KT>
+__global__ void block_sort_kernel(void *store, const uint2 *bins, const uint32_t *list, uint32_t count,
+                                  uint32_t cap_pow2)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KT *sh = reinterpret_cast<KT *>(smem_raw);
+    for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
+        uint2 bi = bins[list[w]];
+        KT *run = leaf_run<KT>(store, bi);
+        uint32_t n = bi.y;
+        uint32_t P = 1;
+        while (P < n) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < n ? run[i] : pad_key<KT>();
+        __syncthreads();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    uint32_t p = i ^ j;
+                    if (p > i) {
+                        KT a = sh[i], b = sh[p];
+                        bool up = (i & k) == 0;
+                        if ((a > b) == up) { sh[i] = b; sh[p] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) run[i] = sh[i];
+        __syncthreads();
+    }
+    (void)cap_pow2;
+}
+
+// Bins larger than shared memory: the same network on a power-of-two scratch
+// copy in global memory, one bin per launch.
+template <typename KT>
+__global__ void global_sort_stage_kernel(KT *buf, uint32_t P, uint32_t k, uint32_t j)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        uint32_t p = i ^ j;
+        if (p > i) {
+            KT a = buf[i], b = buf[p];
+            bool up = (i & k) == 0;
+            if ((a > b) == up) { buf[i] = b; buf[p] = a; }
+        }
+    }
+}
+
+template <typename KT>
+__global__ void copy_pad_kernel(const KT *src, uint32_t n, KT *dst, uint32_t P)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x)
+        dst[i] = i < n ? src[i] : pad_key<KT>();
+}
+
+template <typename KT>
+__global__ void copy_back_kernel(const KT *src, uint32_t n, KT *dst)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+// Pad every bin's last leaf with +inf and fill its internal separators: the
+// separator of child j at level l-1 of a level-l node is the largest key of
+// the child's subtree, key[min((j+1) K^l, n) - 1], or +inf past the end.
+template <typename KT>
+__global__ void index_kernel(void *store, const uint2 *bins, int64_t nbins)
+{
+    constexpr int LK = KeyT<KT>::LK;
+    constexpr int K = KeyT<KT>::K;
+    const int lane = threadIdx.x & 31;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
+         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        uint2 bi = bins[g];
+        uint32_t n = bi.y;
+        if (n == 0) continue;
+        KT *nodes = reinterpret_cast<KT *>(store) + ((size_t)bi.x << LK);
+        uint32_t L0 = ((n - 1) >> LK) + 1;
+        int h = tree_levels(L0, LK);
+        uint32_t internal = internal_nodes(n, LK);
+        KT *run = nodes + ((size_t)internal << LK);
+        for (uint32_t i = n + lane; i < (L0 << LK); i += 32) run[i] = pad_key<KT>();
+        uint32_t off = 0;
+        for (int l = h; l >= 1; --l) {
+            uint32_t cnt = ((L0 - 1) >> (LK * l)) + 1;
+            for (uint32_t slot = lane; slot < (cnt << LK); slot += 32) {
+                uint64_t j = slot;  // child index at level l - 1
+                uint64_t first = j << (LK * l);
+                KT v;
+                if (first >= n) v = pad_key<KT>();
+                else {
+                    uint64_t last = (j + 1) << (LK * l);
+                    if (last > n) last = n;
+                    v = run[last - 1];
+                }
+                nodes[((size_t)(off) << LK) + slot] = v;
+            }
+            off += cnt;
+        }
+    }
+}
+
+// ------------------------------------------------------------ host
+
+static unsigned grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 64) b = 152 * 64;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+struct Buf {
+    void *p = nullptr;
+    ~Buf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+    template <typename T> T *as() { return reinterpret_cast<T *>(p); }
+};
+
+// Sort every bin's leaf run (keys already scattered), pad and index.
+template <typename KT>
+static cddt_status sort_and_index(cddt_s *h, cudaStream_t st)
+{
+    int64_t nb = h->total_bins;
+    Buf lists, list_n;
+    CDDT_CUDA(lists.alloc(sizeof(uint32_t) * 4 * (size_t)nb));
+    CDDT_CUDA(list_n.alloc(sizeof(uint32_t) * 4));
+    CDDT_CUDA(cudaMemsetAsync(list_n.p, 0, sizeof(uint32_t) * 4, st));
+    classify_kernel<<<grid_for(nb, 256), 256, 0, st>>>(h->bins, nb, lists.as<uint32_t>(),
+                                                       list_n.as<uint32_t>(), nb);
+    uint32_t cnt[4];
+    CDDT_CUDA(cudaMemcpyAsync(cnt, list_n.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    CDDT_CUDA(cudaStreamSynchronize(st));
+    uint32_t *L = lists.as<uint32_t>();
+    if (cnt[0]) warp_sort_kernel<KT><<<grid_for((int64_t)cnt[0] * 32, 256), 256, 0, st>>>(h->store, h->bins, L, cnt[0]);
+    if (cnt[1]) {
+        size_t sm = sizeof(KT) * kBlockSortMax;
+        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[1], 152 * 8), 256, sm, st>>>(h->store, h->bins, L + nb, cnt[1], kBlockSortMax);
+    }
+    if (cnt[2]) {
+        size_t sm = sizeof(KT) * kBigSortMax;
+        CDDT_CUDA(cudaFuncSetAttribute(block_sort_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[2], 152 * 2), 1024, sm, st>>>(h->store, h->bins, L + 2 * nb, cnt[2], kBigSortMax);
+    }
+    if (cnt[3]) {
+        std::vector<uint32_t> big(cnt[3]);
+        CDDT_CUDA(cudaMemcpyAsync(big.data(), L + 3 * nb, sizeof(uint32_t) * cnt[3], cudaMemcpyDeviceToHost, st));
+        std::vector<uint2> bis(cnt[3]);
+        CDDT_CUDA(cudaStreamSynchronize(st));
+        for (uint32_t q = 0; q < cnt[3]; ++q)
+            CDDT_CUDA(cudaMemcpy(&bis[q], h->bins + big[q], sizeof(uint2), cudaMemcpyDeviceToHost));
+        uint32_t Pmax = 1;
+        for (auto &b : bis) while (Pmax < b.y) Pmax <<= 1;
+        Buf tmp;
+        CDDT_CUDA(tmp.alloc(sizeof(KT) * (size_t)Pmax));
+        constexpr int LK = KeyT<KT>::LK;
+        for (auto &b : bis) {
+            uint32_t P = 1;
+            while (P < b.y) P <<= 1;
+            KT *run = reinterpret_cast<KT *>(h->store) + ((size_t)(b.x + internal_nodes(b.y, LK)) << LK);
+            copy_pad_kernel<KT><<<grid_for(P, 256), 256, 0, st>>>(run, b.y, tmp.as<KT>(), P);
+            for (uint32_t k = 2; k <= P; k <<= 1)
+                for (uint32_t j = k >> 1; j > 0; j >>= 1)
+                    global_sort_stage_kernel<KT><<<grid_for(P, 256), 256, 0, st>>>(tmp.as<KT>(), P, k, j);
+            copy_back_kernel<KT><<<grid_for(b.y, 256), 256, 0, st>>>(tmp.as<KT>(), b.y, run);
+        }
+        CDDT_CUDA(cudaStreamSynchronize(st));
+    }
+    index_kernel<KT><<<grid_for(nb * 32, 256), 256, 0, st>>>(h->store, h->bins, nb);
+    CDDT_CUDA(cudaGetLastError());
+    return CDDT_OK;
+}
+
+cddt_status sort_and_index_any(cddt_s *h, cudaStream_t st)
+{
+    return h->u16 ? sort_and_index<uint16_t>(h, st) : sort_and_index<float>(h, st);
+}
+
+// Lay out bins from per-bin counts: node offsets, bins[], store allocation.
+// count_dev is consumed (overwritten).  Synchronises `st`.
+cddt_status layout_bins(cddt_s *h, uint32_t *count_dev, cudaStream_t st, void **store_out,
+                        int64_t *nodes_out, int64_t extra_nodes)
+{
+    int64_t nb = h->total_bins;
+    const int LK = h->u16 ? 4 : 3;
+    Buf nodes, scratch, tot, mx;
+    CDDT_CUDA(nodes.alloc(sizeof(uint32_t) * (size_t)nb));
+    CDDT_CUDA(scratch.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nb)));
+    CDDT_CUDA(tot.alloc(sizeof(uint64_t) * 2));
+    CDDT_CUDA(mx.alloc(sizeof(unsigned long long)));
+    CDDT_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), st));
+    if (LK == 3) nodes_kernel<3><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
+    else nodes_kernel<4><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
+    exclusive_scan_u32(nodes.as<uint32_t>(), nodes.as<uint32_t>(), nb, scratch.as<uint64_t>(), tot.as<uint64_t>(), st);
+    // total zero points: scan the counts too (into scratch space of `tot`)
+    Buf zscratch;
+    CDDT_CUDA(zscratch.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nb)));
+    {
+        int64_t nblk = (nb + kScanTile - 1) / kScanTile;
+        if (nblk) {
+            scan_reduce_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(count_dev, nb, zscratch.as<uint64_t>());
+            scan_partials_kernel<<<1, 1024, 0, st>>>(zscratch.as<uint64_t>(), nblk, tot.as<uint64_t>() + 1);
+        } else {
+            CDDT_CUDA(cudaMemsetAsync(tot.as<uint64_t>() + 1, 0, sizeof(uint64_t), st));
+        }
+    }
+    bins_kernel<<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nodes.as<uint32_t>(), nb, h->bins,
+                                                   mx.as<unsigned long long>());
+    uint64_t host_tot[2];
+    unsigned long long host_mx = 0;
+    CDDT_CUDA(cudaMemcpyAsync(host_tot, tot.p, sizeof(host_tot), cudaMemcpyDeviceToHost, st));
+    CDDT_CUDA(cudaMemcpyAsync(&host_mx, mx.p, sizeof(host_mx), cudaMemcpyDeviceToHost, st));
+    CDDT_CUDA(cudaStreamSynchronize(st));
+    CDDT_CUDA(cudaGetLastError());
+    if (host_tot[0] + (uint64_t)extra_nodes > 0xffffffffull) return CDDT_ERR_OOM;
+    int64_t alloc_nodes = (int64_t)host_tot[0] + extra_nodes;
+    void *store = nullptr;
+    CDDT_CUDA(cudaMalloc(&store, (size_t)std::max<int64_t>(alloc_nodes, 1) * 32));
+    *store_out = store;
+    *nodes_out = (int64_t)host_tot[0];
+    h->n_zp = (int64_t)host_tot[1];
+    h->max_bin = (int64_t)host_mx;
+    return CDDT_OK;
+}
+
+// Slice tables (readings S1-S3, S7), computed in double on the host.
+static void slice_tables(cddt_s *h, std::vector<SliceInfo> &out)
+{
+    const double PI = 3.14159265358979323846;
+    out.resize(h->S);
+    double cx[4] = {-0.5, h->W - 0.5, -0.5, h->W - 0.5};
+    double cy[4] = {-0.5, -0.5, h->H - 0.5, h->H - 0.5};
+    uint32_t base = 0;
+    for (int s = 0; s < h->S; ++s) {
+        double ang = (2.0 * PI * (double)s) / (double)h->N;
+        float c = (float)std::cos(ang), sn = (float)std::sin(ang);
+        if (s == 0) { c = 1.0f; sn = 0.0f; }
+        if (4 * s == h->N) { c = 0.0f; sn = 1.0f; }
+        double ymin = 1e300, ymax = -1e300, xmin = 1e300;
+        for (int q = 0; q < 4; ++q) {
+            double yr = cy[q] * (double)c - cx[q] * (double)sn;
+            double xr = cx[q] * (double)c + cy[q] * (double)sn;
+            ymin = std::min(ymin, yr);
+            ymax = std::max(ymax, yr);
+            xmin = std::min(xmin, xr);
+        }
+        SliceInfo si{};
+        si.c = c;
+        si.s = sn;
+        double T = std::ceil(-ymin) + 1.0;
+        si.T = (int32_t)T;
+        si.nb = (int32_t)(std::ceil(ymax + T) + 2.0);
+        si.sbase = base;
+        si.X = (float)(std::ceil(-xmin) + 1.0);
+        base += (uint32_t)si.nb;
+        out[s] = si;
+    }
+    h->total_bins = base;
+}
+
+// Build the store from the handle's edge map (used by build and by the
+// update's rebuild-free path for tests).
+cddt_status construct(cddt_s *h, cudaStream_t st)
+{
+    const int64_t ncell = (int64_t)h->W * h->H;
+    const int threads = 256;
+    // edge cell list
+    int64_t nblk = (ncell + threads - 1) / threads;
+    Buf bcount, boff, scratch, tot, cells;
+    CDDT_CUDA(bcount.alloc(sizeof(uint32_t) * (size_t)nblk));
+    CDDT_CUDA(boff.alloc(sizeof(uint32_t) * (size_t)nblk));
+    CDDT_CUDA(scratch.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nblk)));
+    CDDT_CUDA(tot.alloc(sizeof(uint64_t)));
+    flag_count_kernel<<<(unsigned)nblk, threads, 0, st>>>(h->edge, ncell, bcount.as<uint32_t>());
+    exclusive_scan_u32(bcount.as<uint32_t>(), boff.as<uint32_t>(), nblk, scratch.as<uint64_t>(), tot.as<uint64_t>(), st);
+    uint64_t E = 0;
+    CDDT_CUDA(cudaMemcpyAsync(&E, tot.p, sizeof(E), cudaMemcpyDeviceToHost, st));
+    CDDT_CUDA(cudaStreamSynchronize(st));
+    h->n_edge = (int64_t)E;
+    CDDT_CUDA(cells.alloc(sizeof(uint32_t) * (size_t)std::max<uint64_t>(E, 1)));
+    flag_write_kernel<<<(unsigned)nblk, threads, 0, st>>>(h->edge, ncell, boff.as<uint32_t>(), cells.as<uint32_t>());
+    // counts
+    Buf count;
+    CDDT_CUDA(count.alloc(sizeof(uint32_t) * (size_t)h->total_bins));
+    CDDT_CUDA(cudaMemsetAsync(count.p, 0, sizeof(uint32_t) * (size_t)h->total_bins, st));
+    int64_t work = (int64_t)E * h->S;
+    if (work) count_kernel<<<grid_for(work, threads), threads, 0, st>>>(cells.as<uint32_t>(), (int64_t)E, h->W, h->slices, h->S, count.as<uint32_t>());
+    void *store = nullptr;
+    int64_t nodes = 0;
+    cddt_status rc = layout_bins(h, count.as<uint32_t>(), st, &store, &nodes, 0);
+    if (rc != CDDT_OK) return rc;
+    if (h->store) cudaFree(h->store);
+    h->store = store;
+    h->store_nodes = nodes;
+    h->store_cap = std::max<int64_t>(nodes, 1);
+    // scatter
+    CDDT_CUDA(cudaMemsetAsync(count.p, 0, sizeof(uint32_t) * (size_t)h->total_bins, st));
+    if (work) {
+        if (h->u16)
+            scatter_kernel<uint16_t><<<grid_for(work, threads), threads, 0, st>>>(cells.as<uint32_t>(), (int64_t)E, h->W, h->slices, h->S, h->bins, count.as<uint32_t>(), h->store, h->Q);
+        else
+            scatter_kernel<float><<<grid_for(work, threads), threads, 0, st>>>(cells.as<uint32_t>(), (int64_t)E, h->W, h->slices, h->S, h->bins, count.as<uint32_t>(), h->store, h->Q);
+    }
+    CDDT_CUDA(cudaGetLastError());
+    rc = sort_and_index_any(h, st);
+    if (rc != CDDT_OK) return rc;
+    CDDT_CUDA(cudaStreamSynchronize(st));
+    return CDDT_OK;
+}
+
+cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st)
+{
+    std::vector<SliceInfo> tab;
+    slice_tables(h, tab);
+    if (h->total_bins > 0xffffffffll) return CDDT_ERR_ARG;
+    if (h->u16) {
+        double diag = std::sqrt((double)h->W * h->W + (double)h->H * h->H);
+        double q = 65535.0 / (diag + 4.0);
+        if (q < 1.0) return CDDT_ERR_ARG;
+        int e;
+        std::frexp(q, &e);
+        h->Q = (float)std::ldexp(1.0, e - 1);
+        h->invQ = (float)(1.0 / std::ldexp(1.0, e - 1));
+    }
+    const int64_t ncell = (int64_t)h->W * h->H;
+    CDDT_CUDA(cudaMalloc(&h->slices, sizeof(SliceInfo) * h->S));
+    CDDT_CUDA(cudaMalloc(&h->bins, sizeof(uint2) * (size_t)std::max<int64_t>(h->total_bins, 1)));
+    CDDT_CUDA(cudaMalloc(&h->grid, (size_t)ncell));
+    CDDT_CUDA(cudaMalloc(&h->edge, (size_t)ncell));
+    CDDT_CUDA(cudaMalloc(&h->status, sizeof(int)));
+    CDDT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    CDDT_CUDA(cudaMemcpyAsync(h->slices, tab.data(), sizeof(SliceInfo) * h->S, cudaMemcpyHostToDevice, st));
+    normalise_grid_kernel<<<grid_for(ncell, 256), 256, 0, st>>>(grid_dev, h->grid, ncell);
+    edge_map_kernel<<<grid_for(ncell, 256), 256, 0, st>>>(h->grid, h->edge, h->W, h->H);
+    CDDT_CUDA(cudaGetLastError());
+    return construct(h, st);
+}
+
+}  // namespace cddt

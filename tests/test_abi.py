@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/cddt.h declares.  Host-side argument checks answer without a GPU
+(no compute call is made here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_01167_gb300 import cddt
+    return cddt.load(build_if_missing=True)
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cddt.h")).read()
+    return sorted(set(re.findall(r"^CDDT_API[^(]*?\b(cddt_\w+)\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("cddt_build", "cddt_prune", "cddt_update_cells", "cddt_calc_range_many",
+                     "cddt_sensor_weights", "cddt_sensor_weights_backward", "cddt_destroy",
+                     "cddt_export", "cddt_get_stats", "cddt_plan_create", "cddt_plan_run"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1705_01167_gb300 import cddt
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) == set(cddt.EXPORTED)
+    assert lib.cddt_version() == 1
+
+
+def test_status_strings(lib):
+    from paper_1705_01167_gb300 import cddt
+    for s in range(7):
+        assert len(cddt.status_string(s)) > 0
+    assert "unknown" in cddt.status_string(99)
+
+
+def test_host_side_argument_errors(lib):
+    """Invalid arguments are rejected on the host before any device call."""
+    from paper_1705_01167_gb300 import cddt
+    h = C.c_void_p()
+    fake = C.c_void_p(0x1000)
+    ARG = cddt.CDDT_ERR_ARG
+    assert lib.cddt_build(fake, 0, 10, 8, 10.0, 0, None, C.byref(h)) == ARG
+    assert lib.cddt_build(fake, 10, 10, 7, 10.0, 0, None, C.byref(h)) == ARG
+    assert lib.cddt_build(fake, 10, 10, 8, -1.0, 0, None, C.byref(h)) == ARG
+    assert lib.cddt_build(fake, 10, 10, 8, 10.0, 8, None, C.byref(h)) == ARG
+    assert lib.cddt_build(None, 10, 10, 8, 10.0, 0, None, C.byref(h)) == ARG
+    assert lib.cddt_build(fake, 40000, 10, 8, 10.0, 0, None, C.byref(h)) == ARG
+    assert lib.cddt_build(fake, 10, 10, 8, 10.0, 0, None, None) == ARG
+    assert lib.cddt_destroy(None) == cddt.CDDT_OK
+    assert lib.cddt_prune(None, None) == ARG
+    assert lib.cddt_calc_range_many(None, fake, fake, 1, 0, None) == ARG
+    assert lib.cddt_set_search(None, 0) == ARG
+    assert lib.cddt_plan_create(None, 0, None, C.byref(h)) == ARG
+    assert lib.cddt_plan_destroy(None) == cddt.CDDT_OK
