@@ -1,0 +1,476 @@
+"""Benchmark: CDDT ray casts per second fused with the beam sensor model.
+
+Default workload (the 2000 x 2000 corridor configuration): a seeded
+recursive-division map (walls 1-3 cells, doors 3-20, ~8 % occupied),
+theta_disc = 200, max range 1000 cells.  A ground-truth pose random-walks for
+200 filter steps; each step has 2500 particles drawn around it and its own
+61-beam, 270-degree scan.  One benchmark step weights all 200 filter steps
+(500,000 particles x 61 beams = 30.5 M ray casts) in one persistent batched
+launch; the CDDT (about 290 MB with its search trees) is resident in HBM and
+L2 is flushed between steps.  Extra keys report the same work as 200
+per-filter launches, as a CUDA graph, on the pruned CDDT, and a 10 M-query
+calc_range_many sweep.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {cddt,reference}]
+
+`--impl reference` times the CPU oracle (the paper's plain CDDT: sorted
+bins, binary search) on the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1705_01167_gb300 import synth  # noqa: E402
+
+METRIC = "ray casts/s fused w/ sensor model on 1 GB300, % of L2/HBM gather roofline"
+UNIT = "ray casts/s"
+W_MAP = H_MAP = 2000
+THETA = 200
+MAX_RANGE = 1000.0
+STEPS = 200
+PARTICLES = 2500
+BEAMS = 61
+SWEEP = 10_000_000
+WORKLOAD = (f"corridor {W_MAP}x{H_MAP} (~8% occupied, walls 1-3, doors 3-20), theta_disc {THETA}, "
+            f"max range {MAX_RANGE:g}; {STEPS} filter steps x {PARTICLES} particles x {BEAMS} beams "
+            f"(270 deg) per benchmark step, one batched launch")
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_workload():
+    """Seeded inputs of the corridor configuration (host arrays)."""
+    g = synth.corridor_map(W_MAP, H_MAP)
+    gt = synth.gt_walk(g, STEPS, seed=synth.SEED_PARTICLES)
+    parts = np.stack([synth.tracking_particles(gt[t], PARTICLES, seed=synth.SEED_PARTICLES + 1000 + t)
+                      for t in range(STEPS)])
+    bo = synth.beam_offsets(BEAMS)
+    D = synth.pair_offset(BEAMS)
+    noise = np.stack([synth.noise(BEAMS, 2.0, seed=synth.SEED_OBS + t) for t in range(STEPS)])
+    sweep = synth.uniform_queries(g, SWEEP, seed=synth.SEED_PARTICLES + 7)
+    return dict(grid=g, gt=gt, parts=parts.astype(np.float32), bo=bo, D=D, noise=noise, sweep=sweep)
+
+
+def gt_queries(gt, bo):
+    return np.concatenate([np.stack([np.full(bo.size, p[0]), np.full(bo.size, p[1]),
+                                     (np.float32(p[2]) + bo)], 1) for p in gt]).astype(np.float32)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1705_01167_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, launch_units: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    launch's units, when it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_sha") != kernel_source_sha():
+        return None
+    return d["dram_bytes_per_unit"] * launch_units
+
+
+def algorithmic_bytes(work: dict, P: int) -> int:
+    """Algorithmic bytes of one sensor launch: per search 8 B of bin offsets
+    plus 4 B per probe of a sorted binary search (ceil(log2(k_b + 1)) probes),
+    4 B per paired reverse beam, 12 B pose + 1 B occupancy + 4 B log-weight
+    per particle."""
+    return 8 * work["traversals"] + 4 * work["probes"] + 4 * work["paired"] + 17 * P
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def cpu_oracle_run(wl, steps, cores):
+    """The CPU oracle (sorted bins, binary search, float64 beam model) over
+    `steps` of the filter steps on `cores` host threads.  Returns (seconds,
+    ray casts)."""
+    from oracle import oracle as O
+    o = wl.get("_oracle")
+    if o is None:
+        o = O.OracleCDDT(wl["grid"], THETA, MAX_RANGE)
+        wl["_oracle"] = o
+    m = O.beam_model(MAX_RANGE)
+    obs = wl["obs"]
+    t0 = time.perf_counter()
+    for t in range(steps):
+        o.sensor_weights(wl["parts"][t], wl["bo"], obs[t], m, nthreads=cores)
+    return time.perf_counter() - t0, steps * PARTICLES * BEAMS
+
+
+def oracle_obs(wl):
+    from oracle import oracle as O
+    o = O.OracleCDDT(wl["grid"], THETA, MAX_RANGE)
+    wl["_oracle"] = o
+    r = o.calc_range(gt_queries(wl["gt"], wl["bo"]), nthreads=os.cpu_count() or 1)
+    wl["obs"] = np.clip(r.reshape(STEPS, BEAMS) + wl["noise"], 0, MAX_RANGE).astype(np.float32)
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    wl = make_workload()
+    oracle_obs(wl)
+    sample_steps = 40  # a bounded sample of the 200 filter steps per benchmark step
+    for _ in range(args.warmup):
+        cpu_oracle_run(wl, sample_steps, cores)
+    tot, rays = 0.0, 0
+    for _ in range(args.steps):
+        dt, r = cpu_oracle_run(wl, sample_steps, cores)
+        tot += dt
+        rays += r
+    value = rays / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{sample_steps} of {STEPS} filter steps per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample_steps} filter steps x {PARTICLES} particles x {BEAMS} beams per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    from paper_1705_01167_gb300 import cddt as G
+    G.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    wl = make_workload()
+    bo = wl["bo"]
+    D = wl["D"]
+    grid = torch.from_numpy(wl["grid"]).to(dev)
+    t0 = time.perf_counter()
+    d = G.CDDT(grid, THETA, MAX_RANGE)
+    torch.cuda.synchronize()
+    build_wall = time.perf_counter() - t0
+    st0 = d.stats()
+    # observations: cast from the ground truth pose of each step, plus noise
+    r = d.calc_range_many(torch.from_numpy(gt_queries(wl["gt"], bo)).to(dev)).cpu().numpy()
+    obs = np.clip(r.reshape(STEPS, BEAMS) + wl["noise"], 0, MAX_RANGE).astype(np.float32)
+    wl["obs"] = obs
+    parts_d = torch.from_numpy(wl["parts"].reshape(-1, 3)).to(dev).contiguous()
+    bo_d = torch.from_numpy(bo).to(dev)
+    obs_d = torch.from_numpy(obs).to(dev).contiguous()
+    logw_d = torch.empty(STEPS * PARTICLES, dtype=torch.float32, device=dev)
+    m = G.beam_model(MAX_RANGE)
+    P = PARTICLES
+
+    def filters_for(handle):
+        return [dict(map=handle, particles=parts_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t],
+                     model=m, logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(STEPS)]
+
+    plan = G.Plan(filters_for(d))
+    shape = plan.autotune()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for i in range(k):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return [a.elapsed_time(b) for a, b in ev]
+
+    rays_per_step = STEPS * PARTICLES * BEAMS
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: plan.run(), args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_step = max_over_ranks(world, sum(ms) / len(ms))
+    value = world * rays_per_step / (ms_step * 1e-3)
+
+    # work figures and roofline of the dominant kernel (the batched launch)
+    work = {k: 0 for k in ("traversals", "beams", "nonempty", "probes", "paired", "passed")}
+    for t in range(STEPS):
+        w = d.sensor_work(parts_d[t * P:(t + 1) * P], bo_d, D)
+        for k in work:
+            work[k] += w[k]
+    alg_bytes = algorithmic_bytes(work, STEPS * P)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    traffic = recorded_traffic("batched_kernel", STEPS * P)
+
+    extra = {}
+    # graph replay of the same launch
+    ms_g = timed(lambda: plan.launch_graph(), max(3, args.steps // 2), 2)
+    extra["graph_rays_per_s"] = rays_per_step / (statistics.mean(ms_g) * 1e-3)
+
+    # 200 per-filter launches of cddt_sensor_weights (the plain, unbatched path)
+    def sequential():
+        for t in range(STEPS):
+            d.sensor_weights(parts_d[t * P:(t + 1) * P], bo_d, obs_d[t], m, D, logw=logw_d[t * P:(t + 1) * P])
+    ms_s = timed(sequential, max(3, args.steps // 2), 2)
+    extra["sequential_rays_per_s"] = rays_per_step / (statistics.mean(ms_s) * 1e-3)
+    extra["batched_speedup_vs_sequential"] = statistics.mean(ms_s) / ms_step
+
+    # binary-search layout on the same data
+    d.set_search(G.SEARCH_BINARY)
+    ms_b = timed(lambda: plan.run(), max(3, args.steps // 2), 2)
+    d.set_search(G.SEARCH_TREE)
+    extra["binary_search_rays_per_s"] = rays_per_step / (statistics.mean(ms_b) * 1e-3)
+
+    # 10 M-query sweep, uniform over free space
+    sw = torch.from_numpy(wl["sweep"]).to(dev)
+    out = torch.empty(SWEEP, dtype=torch.float32, device=dev)
+    ms_u = timed(lambda: d.calc_range_many(sw, out=out), 5, 2)
+    ms_o = timed(lambda: d.calc_range_many(sw, sort_by_slice=True, out=out), 5, 2)
+    extra["sweep_rays_per_s"] = SWEEP / (statistics.mean(ms_u) * 1e-3)
+    extra["sweep_sorted_rays_per_s"] = SWEEP / (statistics.mean(ms_o) * 1e-3)
+
+    # pruned CDDT
+    dp = G.CDDT(grid, THETA, MAX_RANGE)
+    try:
+        dp.prune()
+        stp = dp.stats()
+        plan_p = G.Plan(filters_for(dp))
+        plan_p.set_shape(**shape)
+        ms_p = timed(lambda: plan_p.run(), max(3, args.steps // 2), 2)
+        extra["pruned_rays_per_s"] = rays_per_step / (statistics.mean(ms_p) * 1e-3)
+        extra["prune_ms"] = stp["prune_ms"]
+        extra["pruned_zero_points"] = stp["n_zero_points"]
+        ms_pu = timed(lambda: dp.calc_range_many(sw, out=out), 5, 2)
+        extra["pruned_sweep_rays_per_s"] = SWEEP / (statistics.mean(ms_pu) * 1e-3)
+        plan_p.close()
+    except G.CDDTError as e:
+        extra["pruned"] = f"unavailable: {e}"
+
+    # end to end through the public API from pinned host buffers
+    parts_h = torch.from_numpy(wl["parts"].reshape(-1, 3)).pin_memory()
+    obs_h = torch.from_numpy(obs).pin_memory()
+    logw_h = torch.empty(STEPS * P, dtype=torch.float32).pin_memory()
+
+    def e2e():
+        parts_d.copy_(parts_h, non_blocking=True)
+        obs_d.copy_(obs_h, non_blocking=True)
+        plan.run()
+        logw_h.copy_(logw_d, non_blocking=True)
+    ms_e = timed(e2e, max(3, args.steps // 2), 2)
+    e2e_ms = max_over_ranks(world, statistics.mean(ms_e))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
+                       "inputs": "resident in HBM", "launch": f"persistent batched, autotuned {shape}",
+                       "zero_points": st0["n_zero_points"], "store_bytes": st0["store_bytes"],
+                       "occupancy": round(synth.occupancy(wl["grid"]), 4)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "batched_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                         "work": work},
+            "e2e": {"value": world * rays_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(parts_h.numel() * 4 + obs_h.numel() * 4),
+                    "d2h_bytes_per_step": int(logw_h.numel() * 4)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "build_ms": st0["build_ms"], "build_wall_s": build_wall,
+            **extra,
+        }
+        if not args.no_cpu:
+            cores = os.cpu_count() or 1
+            oracle_obs_wl = dict(wl)
+            oracle_obs_wl.pop("_oracle", None)
+            sample = 40
+            dt, rays = cpu_oracle_run(oracle_obs_wl, sample, cores)
+            line["cpu_baseline"] = {"value": rays / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": f"{sample} of {STEPS} filter steps ({rays} ray casts), "
+                                              f"oracle sensor weights, OpenMP over particles"}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile(args):
+    """A short run for ncu: the batched launch (fixed shape), one per-filter
+    pass and one sweep launch, a few launches each."""
+    import torch
+    from paper_1705_01167_gb300 import cddt as G
+    wl = make_workload()
+    dev = torch.device("cuda", 0)
+    d = G.CDDT(torch.from_numpy(wl["grid"]).to(dev), THETA, MAX_RANGE)
+    bo, D, P = wl["bo"], wl["D"], PARTICLES
+    r = d.calc_range_many(torch.from_numpy(gt_queries(wl["gt"], bo)).to(dev)).cpu().numpy()
+    obs = np.clip(r.reshape(STEPS, BEAMS) + wl["noise"], 0, MAX_RANGE).astype(np.float32)
+    parts_d = torch.from_numpy(wl["parts"].reshape(-1, 3)).to(dev).contiguous()
+    bo_d = torch.from_numpy(bo).to(dev)
+    obs_d = torch.from_numpy(obs).to(dev).contiguous()
+    logw_d = torch.empty(STEPS * P, dtype=torch.float32, device=dev)
+    m = G.beam_model(MAX_RANGE)
+    plan = G.Plan([dict(map=d, particles=parts_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t], model=m,
+                        logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(STEPS)])
+    plan.set_shape(args.shape_tpp, args.shape_ppi, args.shape_block)
+    for _ in range(args.warmup + args.steps):
+        plan.run()
+    for t in range(STEPS):
+        d.sensor_weights(parts_d[t * P:(t + 1) * P], bo_d, obs_d[t], m, D, logw=logw_d[t * P:(t + 1) * P])
+    sw = torch.from_numpy(wl["sweep"]).to(dev)
+    d.calc_range_many(sw)
+    d.calc_range_many(sw, sort_by_slice=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "ok", "logw0": float(logw_d[0]), "zero_points": d.stats()["n_zero_points"]}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
+    ap.add_argument("--shape-tpp", type=int, default=8)
+    ap.add_argument("--shape-ppi", type=int, default=64)
+    ap.add_argument("--shape-block", type=int, default=256)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cddt", choices=["cddt", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.profile:
+        return run_profile(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
