@@ -438,7 +438,7 @@ def run_profile(args):
     m = G.beam_model(MAX_RANGE)
     plan = G.Plan([dict(map=d, particles=parts_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t], model=m,
                         logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(STEPS)])
-    plan.set_shape(args.shape_tpp, args.shape_ppi, args.shape_block)
+    plan.set_shape(args.shape_tpp, args.shape_ppi, args.shape_block, args.shape_regcap)
     for _ in range(args.warmup + args.steps):
         plan.run()
     for t in range(STEPS):
@@ -454,9 +454,10 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
-    ap.add_argument("--shape-tpp", type=int, default=8)
-    ap.add_argument("--shape-ppi", type=int, default=64)
-    ap.add_argument("--shape-block", type=int, default=256)
+    ap.add_argument("--shape-tpp", type=int, default=1)
+    ap.add_argument("--shape-ppi", type=int, default=512)
+    ap.add_argument("--shape-block", type=int, default=512)
+    ap.add_argument("--shape-regcap", type=int, default=0)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)

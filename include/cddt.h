@@ -209,11 +209,14 @@ CDDT_API cddt_status cddt_plan_create(const cddt_filter *filters_host, int32_t n
  * Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_plan_autotune(cddt_plan p, void *stream);
 
-/* Set the launch shape by hand: tpp in {1,2,4,8,16,32} threads per particle,
- * ppi particles per work item (multiple of 32 / tpp), block threads in
- * {64..1024} multiple of 32.  Errors: ARG. */
-CDDT_API cddt_status cddt_plan_set_shape(cddt_plan p, int32_t tpp, int32_t ppi, int32_t block);
-CDDT_API cddt_status cddt_plan_get_shape(cddt_plan p, int32_t *tpp, int32_t *ppi, int32_t *block);
+/* Set the launch shape by hand: tpp in {1,2,4,8} threads per particle, ppi
+ * particles per work item (multiple of 32 / tpp), block threads in {256,
+ * 512}, regcap 0 (registers as the compiler needs) or 1 (capped so that 48
+ * warps stay resident per SM).  Errors: ARG. */
+CDDT_API cddt_status cddt_plan_set_shape(cddt_plan p, int32_t tpp, int32_t ppi, int32_t block,
+                                         int32_t regcap);
+CDDT_API cddt_status cddt_plan_get_shape(cddt_plan p, int32_t *tpp, int32_t *ppi, int32_t *block,
+                                         int32_t *regcap);
 
 /* Run the plan on `stream`: reset the queue and launch once.  Safe to
  * capture in a CUDA graph.  Errors: ARG, CUDA. */

@@ -98,8 +98,8 @@ def load(build_if_missing: bool = True):
             "cddt_sensor_weights_fwd_bwd": (st, [vp, vp, i64, vp, vp, i32, i32, C.POINTER(BeamModel), vp, vp, vp]),
             "cddt_plan_create": (st, [C.POINTER(Filter), i32, vp, C.POINTER(vp)]),
             "cddt_plan_autotune": (st, [vp, vp]),
-            "cddt_plan_set_shape": (st, [vp, i32, i32, i32]),
-            "cddt_plan_get_shape": (st, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+            "cddt_plan_set_shape": (st, [vp, i32, i32, i32, i32]),
+            "cddt_plan_get_shape": (st, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
             "cddt_plan_run": (st, [vp, vp]),
             "cddt_plan_launch_graph": (st, [vp, vp]),
             "cddt_plan_items": (i64, [vp]),
@@ -383,13 +383,14 @@ class Plan:
         _check(load().cddt_plan_autotune(self._h, _stream(stream)), "cddt_plan_autotune")
         return self.shape()
 
-    def set_shape(self, tpp: int, ppi: int, block: int):
-        _check(load().cddt_plan_set_shape(self._h, tpp, ppi, block), "cddt_plan_set_shape")
+    def set_shape(self, tpp: int, ppi: int, block: int, regcap: int = 0):
+        _check(load().cddt_plan_set_shape(self._h, tpp, ppi, block, regcap), "cddt_plan_set_shape")
 
     def shape(self):
-        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
-        _check(load().cddt_plan_get_shape(self._h, C.byref(a), C.byref(b), C.byref(c)), "cddt_plan_get_shape")
-        return {"tpp": a.value, "ppi": b.value, "block": c.value}
+        a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().cddt_plan_get_shape(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
+               "cddt_plan_get_shape")
+        return {"tpp": a.value, "ppi": b.value, "block": c.value, "regcap": d.value}
 
     def run(self, stream=None):
         _check(load().cddt_plan_run(self._h, _stream(stream)), "cddt_plan_run")

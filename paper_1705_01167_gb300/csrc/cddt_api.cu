@@ -32,7 +32,7 @@ void free_handle(cddt_s *h)
 {
     if (!h) return;
     cudaFree(h->slices);
-    cudaFree(h->bins);
+    cudaFree(h->hdr);
     cudaFree(h->store);
     cudaFree(h->grid);
     cudaFree(h->edge);
@@ -258,6 +258,7 @@ cddt_status cddt_set_search(cddt_t h, int32_t search)
 {
     if (!h) return CDDT_ERR_ARG;
     if (search != CDDT_SEARCH_TREE && search != CDDT_SEARCH_BINARY) return CDDT_ERR_ARG;
+    if (h->search != search) h->generation++;
     h->search = search;
     return CDDT_OK;
 }
@@ -278,7 +279,7 @@ cddt_status cddt_get_stats(cddt_t h, cddt_stats *out)
     out->total_bins = h->total_bins;
     out->n_zero_points = h->n_zp;
     out->n_edge_cells = h->n_edge;
-    out->store_bytes = h->store_nodes * 32 + h->total_bins * 8;
+    out->store_bytes = h->store_nodes * 32 + h->total_bins * (int64_t)sizeof(cddt::BinHdr);
     out->max_bin = h->max_bin;
     out->build_ms = h->build_ms;
     out->prune_ms = h->prune_ms;
@@ -309,18 +310,18 @@ cddt_status cddt_export(cddt_t h, int64_t *slice_base_host, int64_t *bin_start_h
         slice_base_host[h->S] = h->total_bins;
     }
     if (!bin_start_host && !zp_host) return CDDT_OK;
-    std::vector<uint2> bins((size_t)h->total_bins);
-    CDDT_CUDA(cudaMemcpy(bins.data(), h->bins, sizeof(uint2) * bins.size(), cudaMemcpyDeviceToHost));
+    std::vector<cddt::BinHdr> hdr((size_t)h->total_bins);
+    CDDT_CUDA(cudaMemcpy(hdr.data(), h->hdr, sizeof(cddt::BinHdr) * hdr.size(), cudaMemcpyDeviceToHost));
     if (bin_start_host) {
         int64_t o = 0;
         for (int64_t g = 0; g < h->total_bins; ++g) {
             bin_start_host[g] = o;
-            o += bins[g].y;
+            o += hdr[g].n;
         }
         bin_start_host[h->total_bins] = o;
     }
     if (!zp_host) return CDDT_OK;
-    const int LK = h->u16 ? 4 : 3;
+    const int LK = h->u16 ? 4 : 3, R = h->u16 ? 12 : 6;
     std::vector<unsigned char> store((size_t)h->store_nodes * 32);
     if (!store.empty())
         CDDT_CUDA(cudaMemcpy(store.data(), h->store, store.size(), cudaMemcpyDeviceToHost));
@@ -328,9 +329,9 @@ cddt_status cddt_export(cddt_t h, int64_t *slice_base_host, int64_t *bin_start_h
     int s = 0;
     for (int64_t g = 0; g < h->total_bins; ++g) {
         while (s + 1 < h->S && (int64_t)sl[s + 1].sbase <= g) ++s;
-        uint32_t n = bins[g].y;
+        uint32_t n = hdr[g].n;
         if (!n) continue;
-        size_t leaf = (size_t)(bins[g].x + cddt::internal_nodes(n, LK)) * 32;
+        size_t leaf = (size_t)(hdr[g].off + cddt::internal_nodes(n, LK, R)) * 32;
         if (h->u16) {
             const uint16_t *k = reinterpret_cast<const uint16_t *>(store.data() + leaf);
             volatile float invQ = h->invQ;

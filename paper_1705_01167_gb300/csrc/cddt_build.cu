@@ -194,29 +194,26 @@ __global__ void count_kernel(const uint32_t *cells, int64_t E, int W, const Slic
     }
 }
 
-template <int LK>
+template <int LK, int R>
 __global__ void nodes_kernel(const uint32_t *count, int64_t nbins, uint32_t *nodes)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
          g += (int64_t)gridDim.x * blockDim.x)
-        nodes[g] = bin_nodes(count[g], LK);
+        nodes[g] = bin_nodes(count[g], LK, R);
 }
 
-__global__ void bins_kernel(const uint32_t *count, const uint32_t *node_off, int64_t nbins, uint2 *bins,
-                            unsigned long long *max_bin)
+__global__ void hdr_kernel(const uint32_t *count, const uint32_t *node_off, int64_t nbins, BinHdr *hdr,
+                           unsigned long long *max_bin)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
          g += (int64_t)gridDim.x * blockDim.x) {
-        bins[g] = make_uint2(node_off[g], count[g]);
+        BinHdr b;
+        b.off = node_off[g];
+        b.n = count[g];
+        for (int q = 0; q < 6; ++q) b.w[q] = 0;
+        hdr[g] = b;
         if (count[g]) atomicMax(max_bin, (unsigned long long)count[g]);
     }
-}
-
-template <typename KT>
-__device__ __forceinline__ KT *leaf_run(void *store, uint2 bi)
-{
-    constexpr int LK = KeyT<KT>::LK;
-    return reinterpret_cast<KT *>(store) + ((size_t)(bi.x + internal_nodes(bi.y, LK)) << LK);
 }
 
 // Scatter: the projected abscissa of every (edge cell, slice, bin) into the
@@ -224,7 +221,7 @@ __device__ __forceinline__ KT *leaf_run(void *store, uint2 bi)
 // the sort that follows).
 template <typename KT>
 __global__ void scatter_kernel(const uint32_t *cells, int64_t E, int W, const SliceInfo *slices, int S,
-                               const uint2 *bins, uint32_t *cursor, void *store, float Q)
+                               const BinHdr *hdr, uint32_t *cursor, void *store, float Q)
 {
     int64_t total = E * S;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -240,9 +237,8 @@ __global__ void scatter_kernel(const uint32_t *cells, int64_t E, int W, const Sl
         if (!cell_bins(yr, half_extent(si.c, si.s), si.T, si.nb, b0, b1)) continue;
         for (int b = b0; b <= b1; ++b) {
             uint32_t g = si.sbase + b;
-            uint2 bi = bins[g];
             uint32_t pos = atomicAdd(cursor + g, 1u);
-            KT *run = leaf_run<KT>(store, bi);
+            KT *run = leaf_run<KT>(store, hdr[g].off, hdr[g].n);
             if (sizeof(KT) == 4)
                 reinterpret_cast<float *>(run)[pos] = xr;
             else
@@ -251,23 +247,31 @@ __global__ void scatter_kernel(const uint32_t *cells, int64_t E, int W, const Sl
     }
 }
 
+static unsigned grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 64) b = 152 * 64;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+
 // ------------------------------------------------------------ segmented sort
 
-template <typename KT> __device__ __forceinline__ KT pad_key();
-template <> __device__ __forceinline__ float pad_key<float>() { return kInf; }
-template <> __device__ __forceinline__ uint16_t pad_key<uint16_t>() { return 0xffffu; }
 
-// Size classes of the per-bin sort.
+// Size classes of the segmented sort.
 constexpr uint32_t kWarpSortMax = 32;
 constexpr uint32_t kBlockSortMax = 2048;
 constexpr uint32_t kBigSortMax = 16384;
 
-__global__ void classify_kernel(const uint2 *bins, int64_t nbins, uint32_t *lists, uint32_t *list_n,
-                                int64_t cap)
+template <typename KT>
+__global__ void classify_kernel(Segs<KT> sg, int64_t nseg, uint32_t *lists, uint32_t *list_n, int64_t cap)
 {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nseg;
          g += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t n = bins[g].y;
+        KT *p;
+        uint32_t n;
+        sg.get((uint32_t)g, p, n);
         int cls;
         if (n <= 1) continue;
         if (n <= kWarpSortMax) cls = 0;
@@ -305,30 +309,30 @@ __device__ __forceinline__ KT warp_bitonic(KT v)
 }
 
 template <typename KT>
-__global__ void warp_sort_kernel(void *store, const uint2 *bins, const uint32_t *list, uint32_t count)
+__global__ void warp_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t count)
 {
     const int lane = threadIdx.x & 31;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count;
          w += (gridDim.x * blockDim.x) >> 5) {
-        uint2 bi = bins[list[w]];
-        KT *run = leaf_run<KT>(store, bi);
-        KT v = lane < (int)bi.y ? run[lane] : pad_key<KT>();
+        KT *run;
+        uint32_t n;
+        sg.get(list[w], run, n);
+        KT v = lane < (int)n ? run[lane] : pad_key<KT>();
         v = warp_bitonic<KT>(v);
-        if (lane < (int)bi.y) run[lane] = v;
+        if (lane < (int)n) run[lane] = v;
     }
 }
 
 // Block bitonic sort in shared memory, padded to a power of two with +inf.
 template <typename KT>
-__global__ void block_sort_kernel(void *store, const uint2 *bins, const uint32_t *list, uint32_t count,
-                                  uint32_t cap_pow2)
+__global__ void block_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t count)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     KT *sh = reinterpret_cast<KT *>(smem_raw);
     for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
-        uint2 bi = bins[list[w]];
-        KT *run = leaf_run<KT>(store, bi);
-        uint32_t n = bi.y;
+        KT *run;
+        uint32_t n;
+        sg.get(list[w], run, n);
         uint32_t P = 1;
         while (P < n) P <<= 1;
         for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < n ? run[i] : pad_key<KT>();
@@ -349,11 +353,10 @@ __global__ void block_sort_kernel(void *store, const uint2 *bins, const uint32_t
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) run[i] = sh[i];
         __syncthreads();
     }
-    (void)cap_pow2;
 }
 
-// Bins larger than shared memory: the same network on a power-of-two scratch
-// copy in global memory, one bin per launch.
+// Segments larger than shared memory: the same network on a power-of-two
+// scratch copy in global memory, one segment at a time.
 template <typename KT>
 __global__ void global_sort_stage_kernel(KT *buf, uint32_t P, uint32_t k, uint32_t j)
 {
@@ -364,6 +367,19 @@ __global__ void global_sort_stage_kernel(KT *buf, uint32_t P, uint32_t k, uint32
             bool up = (i & k) == 0;
             if ((a > b) == up) { buf[i] = b; buf[p] = a; }
         }
+    }
+}
+
+template <typename KT>
+__global__ void seg_info_kernel(Segs<KT> sg, const uint32_t *list, uint32_t count, unsigned long long *ptr,
+                                uint32_t *len)
+{
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
+        KT *p;
+        uint32_t n;
+        sg.get(list[w], p, n);
+        ptr[w] = (unsigned long long)(uintptr_t)p;
+        len[w] = n;
     }
 }
 
@@ -380,120 +396,152 @@ __global__ void copy_back_kernel(const KT *src, uint32_t n, KT *dst)
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
-// Pad every bin's last leaf with +inf and fill its internal separators: the
-// separator of child j at level l-1 of a level-l node is the largest key of
-// the child's subtree, key[min((j+1) K^l, n) - 1], or +inf past the end.
+// Pad every bin's last leaf with +inf and fill its tree: the separator of
+// child j at level l-1 of a level-l node is the largest key of the child's
+// subtree, key[min((j+1) K^l, n) - 1], or +inf past the end; the header holds
+// the root's separators over the top stored level, or the keys themselves
+// when the bin has at most R keys.
 template <typename KT>
-__global__ void index_kernel(void *store, const uint2 *bins, int64_t nbins)
+__device__ __forceinline__ uint32_t key_bits(KT v)
+{
+    if (sizeof(KT) == 4) return __float_as_uint(*reinterpret_cast<const float *>(&v));
+    return (uint32_t)(*reinterpret_cast<const uint16_t *>(&v));
+}
+
+template <typename KT>
+__global__ void index_kernel(void *store, BinHdr *hdr, int64_t nbins)
 {
     constexpr int LK = KeyT<KT>::LK;
-    constexpr int K = KeyT<KT>::K;
+    constexpr int R = KeyT<KT>::R;
     const int lane = threadIdx.x & 31;
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
          g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        uint2 bi = bins[g];
-        uint32_t n = bi.y;
+        const uint32_t n = hdr[g].n, off = hdr[g].off;
         if (n == 0) continue;
-        KT *nodes = reinterpret_cast<KT *>(store) + ((size_t)bi.x << LK);
-        uint32_t L0 = ((n - 1) >> LK) + 1;
-        int h = tree_levels(L0, LK);
-        uint32_t internal = internal_nodes(n, LK);
-        KT *run = nodes + ((size_t)internal << LK);
-        for (uint32_t i = n + lane; i < (L0 << LK); i += 32) run[i] = pad_key<KT>();
-        uint32_t off = 0;
+        KT *run = reinterpret_cast<KT *>(store) + ((size_t)off << LK);
+        const uint32_t L0 = ((n - 1) >> LK) + 1;
+        const int h = run_levels(L0, LK, R);
+        const uint32_t internal = internal_nodes(n, LK, R);
+        KT *leaves = run + ((size_t)internal << LK);
+        for (uint32_t i = n + lane; i < (L0 << LK); i += 32) leaves[i] = pad_key<KT>();
+        uint32_t loff = 0;
         for (int l = h; l >= 1; --l) {
-            uint32_t cnt = ((L0 - 1) >> (LK * l)) + 1;
+            const uint32_t cnt = level_count(L0, LK, l);
             for (uint32_t slot = lane; slot < (cnt << LK); slot += 32) {
-                uint64_t j = slot;  // child index at level l - 1
-                uint64_t first = j << (LK * l);
-                KT v;
-                if (first >= n) v = pad_key<KT>();
-                else {
-                    uint64_t last = (j + 1) << (LK * l);
+                const uint64_t first = (uint64_t)slot << (LK * l);
+                KT v = pad_key<KT>();
+                if (first < n) {
+                    uint64_t last = ((uint64_t)slot + 1) << (LK * l);
                     if (last > n) last = n;
-                    v = run[last - 1];
+                    v = leaves[last - 1];
                 }
-                nodes[((size_t)(off) << LK) + slot] = v;
+                run[((size_t)loff << LK) + slot] = v;
             }
-            off += cnt;
+            loff += cnt;
+        }
+        // header separators: R keys packed into 6 words
+        if (lane < 6) {
+            uint32_t word = 0;
+            const uint32_t cnt_h = level_count(L0, LK, h);
+            const int per = 4 / (int)sizeof(KT);  // keys per word
+            for (int e = 0; e < per; ++e) {
+                const uint32_t q = (uint32_t)(lane * per + e);
+                KT v = pad_key<KT>();
+                if (n <= (uint32_t)R) {
+                    if (q < n) v = leaves[q];
+                } else if (q < cnt_h) {
+                    uint64_t last = ((uint64_t)q + 1) << (LK * (h + 1));
+                    if (last > n) last = n;
+                    v = leaves[last - 1];
+                }
+                word |= key_bits<KT>(v) << (16 * e);
+            }
+            hdr[g].w[lane] = word;
         }
     }
 }
 
 // ------------------------------------------------------------ host
 
-static unsigned grid_for(int64_t n, int threads)
-{
-    int64_t b = (n + threads - 1) / threads;
-    if (b > 152 * 64) b = 152 * 64;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
-
-struct Buf {
-    void *p = nullptr;
-    ~Buf() { if (p) cudaFree(p); }
-    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
-    template <typename T> T *as() { return reinterpret_cast<T *>(p); }
-};
-
-// Sort every bin's leaf run (keys already scattered), pad and index.
+// Sort every segment ascending, by size class.  Synchronises `st`.
 template <typename KT>
-static cddt_status sort_and_index(cddt_s *h, cudaStream_t st)
+cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st)
 {
-    int64_t nb = h->total_bins;
+    if (nseg == 0) return CDDT_OK;
     Buf lists, list_n;
-    CDDT_CUDA(lists.alloc(sizeof(uint32_t) * 4 * (size_t)nb));
+    CDDT_CUDA(lists.alloc(sizeof(uint32_t) * 4 * (size_t)nseg));
     CDDT_CUDA(list_n.alloc(sizeof(uint32_t) * 4));
     CDDT_CUDA(cudaMemsetAsync(list_n.p, 0, sizeof(uint32_t) * 4, st));
-    classify_kernel<<<grid_for(nb, 256), 256, 0, st>>>(h->bins, nb, lists.as<uint32_t>(),
-                                                       list_n.as<uint32_t>(), nb);
+    classify_kernel<KT><<<grid_for(nseg, 256), 256, 0, st>>>(sg, nseg, lists.as<uint32_t>(), list_n.as<uint32_t>(), nseg);
     uint32_t cnt[4];
     CDDT_CUDA(cudaMemcpyAsync(cnt, list_n.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CDDT_CUDA(cudaStreamSynchronize(st));
     uint32_t *L = lists.as<uint32_t>();
-    if (cnt[0]) warp_sort_kernel<KT><<<grid_for((int64_t)cnt[0] * 32, 256), 256, 0, st>>>(h->store, h->bins, L, cnt[0]);
+    if (cnt[0]) warp_sort_kernel<KT><<<grid_for((int64_t)cnt[0] * 32, 256), 256, 0, st>>>(sg, L, cnt[0]);
     if (cnt[1]) {
         size_t sm = sizeof(KT) * kBlockSortMax;
-        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[1], 152 * 8), 256, sm, st>>>(h->store, h->bins, L + nb, cnt[1], kBlockSortMax);
+        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[1], 152 * 8), 256, sm, st>>>(sg, L + nseg, cnt[1]);
     }
     if (cnt[2]) {
         size_t sm = sizeof(KT) * kBigSortMax;
         CDDT_CUDA(cudaFuncSetAttribute(block_sort_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[2], 152 * 2), 1024, sm, st>>>(h->store, h->bins, L + 2 * nb, cnt[2], kBigSortMax);
+        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[2], 152 * 2), 1024, sm, st>>>(sg, L + 2 * nseg, cnt[2]);
     }
     if (cnt[3]) {
-        std::vector<uint32_t> big(cnt[3]);
-        CDDT_CUDA(cudaMemcpyAsync(big.data(), L + 3 * nb, sizeof(uint32_t) * cnt[3], cudaMemcpyDeviceToHost, st));
-        std::vector<uint2> bis(cnt[3]);
+        Buf dptr, dlen;
+        CDDT_CUDA(dptr.alloc(sizeof(unsigned long long) * cnt[3]));
+        CDDT_CUDA(dlen.alloc(sizeof(uint32_t) * cnt[3]));
+        seg_info_kernel<KT><<<grid_for(cnt[3], 256), 256, 0, st>>>(sg, L + 3 * nseg, cnt[3], dptr.as<unsigned long long>(), dlen.as<uint32_t>());
+        std::vector<unsigned long long> ptrs(cnt[3]);
+        std::vector<uint32_t> lens(cnt[3]);
+        CDDT_CUDA(cudaMemcpyAsync(ptrs.data(), dptr.p, sizeof(unsigned long long) * cnt[3], cudaMemcpyDeviceToHost, st));
+        CDDT_CUDA(cudaMemcpyAsync(lens.data(), dlen.p, sizeof(uint32_t) * cnt[3], cudaMemcpyDeviceToHost, st));
         CDDT_CUDA(cudaStreamSynchronize(st));
-        for (uint32_t q = 0; q < cnt[3]; ++q)
-            CDDT_CUDA(cudaMemcpy(&bis[q], h->bins + big[q], sizeof(uint2), cudaMemcpyDeviceToHost));
         uint32_t Pmax = 1;
-        for (auto &b : bis) while (Pmax < b.y) Pmax <<= 1;
+        for (uint32_t n : lens) while (Pmax < n) Pmax <<= 1;
         Buf tmp;
         CDDT_CUDA(tmp.alloc(sizeof(KT) * (size_t)Pmax));
-        constexpr int LK = KeyT<KT>::LK;
-        for (auto &b : bis) {
-            uint32_t P = 1;
-            while (P < b.y) P <<= 1;
-            KT *run = reinterpret_cast<KT *>(h->store) + ((size_t)(b.x + internal_nodes(b.y, LK)) << LK);
-            copy_pad_kernel<KT><<<grid_for(P, 256), 256, 0, st>>>(run, b.y, tmp.as<KT>(), P);
+        for (uint32_t q = 0; q < cnt[3]; ++q) {
+            uint32_t n = lens[q], P = 1;
+            while (P < n) P <<= 1;
+            KT *run = reinterpret_cast<KT *>((uintptr_t)ptrs[q]);
+            copy_pad_kernel<KT><<<grid_for(P, 256), 256, 0, st>>>(run, n, tmp.as<KT>(), P);
             for (uint32_t k = 2; k <= P; k <<= 1)
                 for (uint32_t j = k >> 1; j > 0; j >>= 1)
                     global_sort_stage_kernel<KT><<<grid_for(P, 256), 256, 0, st>>>(tmp.as<KT>(), P, k, j);
-            copy_back_kernel<KT><<<grid_for(b.y, 256), 256, 0, st>>>(tmp.as<KT>(), b.y, run);
+            copy_back_kernel<KT><<<grid_for(n, 256), 256, 0, st>>>(tmp.as<KT>(), n, run);
         }
-        CDDT_CUDA(cudaStreamSynchronize(st));
     }
-    index_kernel<KT><<<grid_for(nb * 32, 256), 256, 0, st>>>(h->store, h->bins, nb);
+    CDDT_CUDA(cudaStreamSynchronize(st));
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;
 }
 
+template cddt_status sort_segments<float>(const Segs<float> &, int64_t, cudaStream_t);
+template cddt_status sort_segments<uint16_t>(const Segs<uint16_t> &, int64_t, cudaStream_t);
+
+cddt_status index_store(cddt_s *h, cudaStream_t st)
+{
+    const int64_t nb = h->total_bins;
+    if (h->u16) index_kernel<uint16_t><<<grid_for(nb * 32, 256), 256, 0, st>>>(h->store, h->hdr, nb);
+    else index_kernel<float><<<grid_for(nb * 32, 256), 256, 0, st>>>(h->store, h->hdr, nb);
+    CDDT_CUDA(cudaGetLastError());
+    return CDDT_OK;
+}
+
+// Sort every bin's leaf run (keys already scattered), pad and index.
 cddt_status sort_and_index_any(cddt_s *h, cudaStream_t st)
 {
-    return h->u16 ? sort_and_index<uint16_t>(h, st) : sort_and_index<float>(h, st);
+    cddt_status rc;
+    if (h->u16) {
+        Segs<uint16_t> sg{h->store, h->hdr, nullptr, nullptr, nullptr};
+        rc = sort_segments<uint16_t>(sg, h->total_bins, st);
+    } else {
+        Segs<float> sg{h->store, h->hdr, nullptr, nullptr, nullptr};
+        rc = sort_segments<float>(sg, h->total_bins, st);
+    }
+    if (rc != CDDT_OK) return rc;
+    return index_store(h, st);
 }
 
 // Lay out bins from per-bin counts: node offsets, bins[], store allocation.
@@ -509,8 +557,8 @@ cddt_status layout_bins(cddt_s *h, uint32_t *count_dev, cudaStream_t st, void **
     CDDT_CUDA(tot.alloc(sizeof(uint64_t) * 2));
     CDDT_CUDA(mx.alloc(sizeof(unsigned long long)));
     CDDT_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), st));
-    if (LK == 3) nodes_kernel<3><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
-    else nodes_kernel<4><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
+    if (LK == 3) nodes_kernel<3, KeyT<float>::R><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
+    else nodes_kernel<4, KeyT<uint16_t>::R><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
     exclusive_scan_u32(nodes.as<uint32_t>(), nodes.as<uint32_t>(), nb, scratch.as<uint64_t>(), tot.as<uint64_t>(), st);
     // total zero points: scan the counts too (into scratch space of `tot`)
     Buf zscratch;
@@ -524,8 +572,8 @@ cddt_status layout_bins(cddt_s *h, uint32_t *count_dev, cudaStream_t st, void **
             CDDT_CUDA(cudaMemsetAsync(tot.as<uint64_t>() + 1, 0, sizeof(uint64_t), st));
         }
     }
-    bins_kernel<<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nodes.as<uint32_t>(), nb, h->bins,
-                                                   mx.as<unsigned long long>());
+    hdr_kernel<<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nodes.as<uint32_t>(), nb, h->hdr,
+                                                  mx.as<unsigned long long>());
     uint64_t host_tot[2];
     unsigned long long host_mx = 0;
     CDDT_CUDA(cudaMemcpyAsync(host_tot, tot.p, sizeof(host_tot), cudaMemcpyDeviceToHost, st));
@@ -617,9 +665,9 @@ cddt_status construct(cddt_s *h, cudaStream_t st)
     CDDT_CUDA(cudaMemsetAsync(count.p, 0, sizeof(uint32_t) * (size_t)h->total_bins, st));
     if (work) {
         if (h->u16)
-            scatter_kernel<uint16_t><<<grid_for(work, threads), threads, 0, st>>>(cells.as<uint32_t>(), (int64_t)E, h->W, h->slices, h->S, h->bins, count.as<uint32_t>(), h->store, h->Q);
+            scatter_kernel<uint16_t><<<grid_for(work, threads), threads, 0, st>>>(cells.as<uint32_t>(), (int64_t)E, h->W, h->slices, h->S, h->hdr, count.as<uint32_t>(), h->store, h->Q);
         else
-            scatter_kernel<float><<<grid_for(work, threads), threads, 0, st>>>(cells.as<uint32_t>(), (int64_t)E, h->W, h->slices, h->S, h->bins, count.as<uint32_t>(), h->store, h->Q);
+            scatter_kernel<float><<<grid_for(work, threads), threads, 0, st>>>(cells.as<uint32_t>(), (int64_t)E, h->W, h->slices, h->S, h->hdr, count.as<uint32_t>(), h->store, h->Q);
     }
     CDDT_CUDA(cudaGetLastError());
     rc = sort_and_index_any(h, st);
@@ -644,7 +692,7 @@ cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st)
     }
     const int64_t ncell = (int64_t)h->W * h->H;
     CDDT_CUDA(cudaMalloc(&h->slices, sizeof(SliceInfo) * h->S));
-    CDDT_CUDA(cudaMalloc(&h->bins, sizeof(uint2) * (size_t)std::max<int64_t>(h->total_bins, 1)));
+    CDDT_CUDA(cudaMalloc(&h->hdr, sizeof(BinHdr) * (size_t)std::max<int64_t>(h->total_bins, 1)));
     CDDT_CUDA(cudaMalloc(&h->grid, (size_t)ncell));
     CDDT_CUDA(cudaMalloc(&h->edge, (size_t)ncell));
     CDDT_CUDA(cudaMalloc(&h->status, sizeof(int)));

@@ -6,16 +6,21 @@
 //  slices  SliceInfo[S]  (S = N/2 stored slices, Section IV-C): cos, sin of
 //          theta_s = 2 pi s / N, the integer bin offset T_s, the bin count,
 //          the first global bin of the slice and the 16-bit offset X_s.
-//  bins    uint2[total_bins]: {node offset in 32-byte nodes, zero-point count n}.
-//  store   32-byte nodes.  Each bin owns a contiguous, 32-byte aligned run of
-//          nodes: the internal nodes of an implicit K-ary search tree (root
-//          first, then each level down) followed by its ceil(n/K) leaf nodes,
-//          which hold the bin's zero points sorted ascending, padded with +inf
-//          (K = 8 float32 keys, or 16 uint16 keys per node).  Separator c of an
-//          internal node at level l is the largest key of its child's subtree
-//          (child j covers keys [j K^l, (j+1) K^l)).  A search reads one node
-//          per level: the root and upper levels are small and stay in L2, the
-//          leaf is one sector.
+//  hdr     BinHdr[total_bins], 32 bytes each: the node offset of the bin's
+//          run, its zero-point count n and the R separators of the root of
+//          the bin's search tree (R = 6 float32 or 12 uint16 keys).  A bin of
+//          at most R keys keeps the keys themselves in the header.
+//  store   32-byte nodes.  Each bin owns a contiguous, 32-byte aligned run:
+//          the internal levels of an implicit K-ary search tree (top level
+//          first) followed by its ceil(n/K) leaf nodes, which hold the bin's
+//          zero points sorted ascending, padded with +inf (K = 8 float32 or
+//          16 uint16 keys per node).  The root (in the header) covers at most
+//          R nodes of the top level.  Separator q of a node is the largest key
+//          of its q-th child's subtree.  A search reads the header, one node
+//          per internal level and one leaf: 3 sectors for the few-hundred-key
+//          bins of a 2000 x 2000 corridor map.  Headers and internal nodes
+//          are read with an L2 evict-last policy so that the stream of leaf
+//          reads does not push them out of L2.
 //  grid    uint8[H][W] occupancy (nonzero = occupied), edge uint8[H][W].
 //
 // Float contract: every float32 step of the projection, binning and range is
@@ -41,9 +46,16 @@ struct __align__(16) SliceInfo {
 };
 
 // Everything a query kernel needs to read one CDDT.
+// Per-bin header (see the layout above).
+struct __align__(32) BinHdr {
+    uint32_t off;   // first node of the bin's run
+    uint32_t n;     // zero points
+    uint32_t w[6];  // root separators, or the keys themselves when n <= R
+};
+
 struct MapView {
     const SliceInfo *slices;
-    const uint2 *bins;
+    const BinHdr *hdr;
     const void *store;
     const uint8_t *grid;
     int32_t W, H, N, S;
@@ -62,6 +74,10 @@ __device__ __forceinline__ bool query_dir(float theta, float inv_step, int N, in
 {
     float t = __fmul_rn(theta, inv_step);
     float tk = floorf(__fadd_rn(t, 0.5f));
+    if (tk >= 0.0f && tk < (float)N) {  // the common case: no wrap
+        k = (int)tk;
+        return true;
+    }
     if (fabsf(tk) < 16777216.0f) {
         int ki = (int)tk % N;
         k = ki < 0 ? ki + N : ki;
@@ -143,234 +159,304 @@ __device__ __forceinline__ float dequantise(uint32_t key, float X, float invQ)
 
 // ------------------------------------------------------------ bin layout
 
-// log2 of keys per 32-byte node.
+// Keys per 32-byte node (K = 2^LK) and root fan-out R held in the header.
 template <typename KT> struct KeyT;
 template <> struct KeyT<float> {
     static constexpr int LK = 3;
     static constexpr int K = 8;
+    static constexpr int R = 6;
 };
 template <> struct KeyT<uint16_t> {
     static constexpr int LK = 4;
     static constexpr int K = 16;
+    static constexpr int R = 12;
 };
 
-__host__ __device__ __forceinline__ int tree_levels(uint32_t L0, int LK)
+// Nodes at level l of a bin with L0 leaves (level 0 = leaves).
+__host__ __device__ __forceinline__ uint32_t level_count(uint32_t L0, int LK, int l)
 {
-    if (L0 <= 1) return 0;
-    uint32_t v = L0 - 1;
-    int bits = 0;
-    while (v) { ++bits; v >>= 1; }
-    return (bits + LK - 1) / LK;
+    return (uint32_t)(((uint64_t)(L0 - 1) >> (LK * l)) + 1);
 }
 
-// Nodes of a bin of n keys: internal nodes above ceil(n/K) leaves.
-__host__ __device__ __forceinline__ uint32_t internal_nodes(uint32_t n, int LK)
+// Internal levels stored in the run: the smallest h whose level fits under
+// the root (at most R nodes).
+__host__ __device__ __forceinline__ int run_levels(uint32_t L0, int LK, int R)
+{
+    int h = 0;
+    while (level_count(L0, LK, h) > (uint32_t)R) ++h;
+    return h;
+}
+
+__host__ __device__ __forceinline__ uint32_t internal_nodes(uint32_t n, int LK, int R)
 {
     if (n == 0) return 0;
     uint32_t L0 = ((n - 1) >> LK) + 1;
-    int h = tree_levels(L0, LK);
+    int h = run_levels(L0, LK, R);
     uint32_t t = 0;
-    for (int l = 1; l <= h; ++l) t += ((L0 - 1) >> (LK * l)) + 1;
+    for (int l = 1; l <= h; ++l) t += level_count(L0, LK, l);
     return t;
 }
-__host__ __device__ __forceinline__ uint32_t bin_nodes(uint32_t n, int LK)
+
+__host__ __device__ __forceinline__ uint32_t bin_nodes(uint32_t n, int LK, int R)
 {
     if (n == 0) return 0;
-    return internal_nodes(n, LK) + ((n - 1) >> LK) + 1;
+    return internal_nodes(n, LK, R) + ((n - 1) >> LK) + 1;
 }
 
-// A 32-byte node read as K keys, compared in float (reading S5 semantics).
-struct NodeF {
-    float v[8];
-    __device__ __forceinline__ void load(const void *p)
-    {
-        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-        float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    }
-};
-
-// Number of keys <= x (Upper) or < x (!Upper) in a node.
-template <bool Upper>
-__device__ __forceinline__ int count_node(const float *v, int K, float x)
+// Loads of a 32-byte node: one 256-bit load (CDDT_LD_V8) or two 128-bit
+// loads; `pol` is an L2 cache policy applied when CDDT_LD_HINT is set.
+#ifndef CDDT_LD_V8
+#define CDDT_LD_V8 1
+#endif
+#ifndef CDDT_LD_HINT
+#define CDDT_LD_HINT 1
+#endif
+__device__ __forceinline__ void ld_node(const void *p, uint32_t (&w)[8])
 {
-    int c = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) c += Upper ? (v[i] <= x) : (v[i] < x);
-    (void)K;
-    return c;
+#if CDDT_LD_V8
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+        : "l"(p));
+#else
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+#endif
 }
-
-__device__ __forceinline__ float pick8(const float *v, int i)
+__device__ __forceinline__ void ld_node(const void *p, uint64_t pol, uint32_t (&w)[8])
 {
-    float r = v[0];
-#pragma unroll
-    for (int k = 1; k < 8; ++k) r = (i == k) ? v[k] : r;
-    return r;
+#if CDDT_LD_HINT && CDDT_LD_V8
+    asm("ld.global.nc.L2::cache_hint.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+        : "l"(p), "l"(pol));
+#elif CDDT_LD_HINT
+    asm("ld.global.nc.L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]) : "l"(reinterpret_cast<const char *>(p) + 16), "l"(pol));
+#else
+    (void)pol;
+    ld_node(p, w);
+#endif
 }
 
-// ---------------------------------------------------------------- search
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t pol = 0;
+#if CDDT_LD_HINT
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#endif
+    return pol;
+}
+
+// Key i of a bin from its leaf run (scalar load).
+template <typename KT>
+__device__ __forceinline__ float bin_key(const MapView &m, uint32_t off, uint32_t n, int i, float X)
+{
+    constexpr int LK = KeyT<KT>::LK;
+    const size_t leaf = (size_t)off + internal_nodes(n, LK, KeyT<KT>::R);
+    if (sizeof(KT) == 4) return __ldg(reinterpret_cast<const float *>(m.store) + (leaf << 3) + i);
+    return dequantise(__ldg(reinterpret_cast<const uint16_t *>(m.store) + (leaf << 4) + i), X, m.invQ);
+}
 
 // Search result: index of the first key > x (Upper) or >= x (!Upper) in the
-// bin, n when none; also the key at that index (when < n) and the key just
-// before it (when the index is > 0), which the paired reverse beam uses.
+// bin, n when none; the key at that index (when < n) and the key just before
+// it (when the index is > 0), which the paired reverse beam uses.
 struct SearchResult {
     int idx;
     float at;    // key[idx]
     float prev;  // key[idx - 1]
 };
 
-// Key i of a bin from the leaf run (scalar load, L1-resident after a search).
+// Comparison of node keys against a query abscissa.  float32 keys compare
+// directly; 16-bit keys compare as integers against the exact threshold:
+// value(key) = key / Q - X is exact in float32, so value(key) <= x iff
+// key <= floor((x + X) Q) and value(key) < x iff key <= ceil((x + X) Q) - 1,
+// evaluated in double where x + X and the product are exact.
+template <typename KT, bool Upper> struct Cmp;
+template <bool Upper> struct Cmp<float, Upper> {
+    float x;
+    __device__ __forceinline__ Cmp(const MapView &, float x_, float) : x(x_) {}
+    __device__ __forceinline__ bool le(uint32_t bits) const
+    {
+        float v = __uint_as_float(bits);
+        return Upper ? (v <= x) : (v < x);
+    }
+};
+template <bool Upper> struct Cmp<uint16_t, Upper> {
+    int t;
+    __device__ __forceinline__ Cmp(const MapView &m, float x, float X)
+    {
+        double xx = ((double)x + (double)X) * (double)m.Q;
+        double tt = Upper ? floor(xx) : ceil(xx) - 1.0;
+        tt = fmax(-1.0, fmin(65536.0, tt));
+        t = (int)tt;
+    }
+    __device__ __forceinline__ bool le(uint32_t key) const { return (int)key <= t; }
+};
+
 template <typename KT>
-__device__ __forceinline__ float bin_key(const MapView &m, const uint2 &bi, uint32_t internal, int i,
-                                         float X)
+__device__ __forceinline__ float key_value(const MapView &m, uint32_t raw, float X)
+{
+    if (sizeof(KT) == 4) return __uint_as_float(raw);
+    return dequantise(raw, X, m.invQ);
+}
+
+// Keys of a node in ascending order as raw 32-bit words (float bits or
+// zero-extended uint16), NK = R for a header, K for a node.
+template <typename KT, int NK>
+__device__ __forceinline__ void unpack(const uint32_t *w, uint32_t (&k)[NK])
 {
     if (sizeof(KT) == 4) {
-        const float *leaf = reinterpret_cast<const float *>(m.store) + ((size_t)(bi.x + internal) << 3);
-        return __ldg(leaf + i);
+#pragma unroll
+        for (int i = 0; i < NK; ++i) k[i] = w[i];
     } else {
-        const uint16_t *leaf =
-            reinterpret_cast<const uint16_t *>(m.store) + ((size_t)(bi.x + internal) << 4);
-        return dequantise(__ldg(leaf + i), X, m.invQ);
+#pragma unroll
+        for (int i = 0; i < NK / 2; ++i) {
+            k[2 * i] = w[i] & 0xffffu;
+            k[2 * i + 1] = w[i] >> 16;
+        }
     }
 }
 
-// Descend the implicit tree of one bin (layout above).
+// Number of a node's keys below the query (keys ascending, padding above).
 template <typename KT, bool Upper>
-__device__ __forceinline__ SearchResult tree_search(const MapView &m, const uint2 &bi, float x, float X)
+__device__ __forceinline__ int count_below(const uint32_t (&w)[8], int from, const Cmp<KT, Upper> &cmp)
+{
+    int c = 0;
+    if (sizeof(KT) == 4) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i >= from) c += cmp.le(w[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i >= from) c += cmp.le(w[i] & 0xffffu) + cmp.le(w[i] >> 16);
+    }
+    return c;
+}
+
+// Key at element index e of an array of KT (scalar load, usually an L1 hit).
+template <typename KT>
+__device__ __forceinline__ float load_key(const MapView &m, const void *base, int64_t e, float X)
+{
+    if (sizeof(KT) == 4) return __ldg(reinterpret_cast<const float *>(base) + e);
+    return dequantise(__ldg(reinterpret_cast<const uint16_t *>(base) + e), X, m.invQ);
+}
+
+// Search one bin through its header and tree (layout above): count the keys
+// below the query at each level, then load the answer's neighbours from the
+// leaf (the leaves are contiguous, so key idx - 1 sits just before key idx).
+// kb receives the bin's size.
+template <typename KT, bool Upper>
+__device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g, float x, float X, uint64_t pol,
+                                                    int &kb)
 {
     constexpr int LK = KeyT<KT>::LK;
     constexpr int K = KeyT<KT>::K;
+    constexpr int R = KeyT<KT>::R;
     SearchResult r;
-    const uint32_t n = bi.y;
     r.idx = 0;
     r.at = kInf;
     r.prev = -kInf;
+    uint32_t w[8];
+    ld_node(m.hdr + g, pol, w);
+    const uint32_t off = w[0], n = w[1];
+    kb = (int)n;
     if (n == 0) return r;
+    const Cmp<KT, Upper> cmp(m, x, X);
+    int c = count_below<KT, Upper>(w, 2, cmp);
+    if (n <= (uint32_t)R) {  // the keys themselves are in the header
+        // padding never compares below an in-map query; the clamp keeps the
+        // answer inside the bin regardless
+        r.idx = min(c, (int)n);
+        const void *keys = reinterpret_cast<const uint32_t *>(m.hdr + g) + 2;
+        if (r.idx < (int)n) r.at = load_key<KT>(m, keys, r.idx, X);
+        if (r.idx > 0) r.prev = load_key<KT>(m, keys, r.idx - 1, X);
+        return r;
+    }
     const uint32_t L0 = ((n - 1) >> LK) + 1;
-    const int h = tree_levels(L0, LK);
-    const char *base = reinterpret_cast<const char *>(m.store) + ((size_t)bi.x << 5);
-    uint32_t off = 0;  // node offset of the current level
-    uint32_t k = 0;    // node index inside the level
-    uint32_t internal = 0;
-    for (int l = h; l >= 1; --l) internal += ((L0 - 1) >> (LK * l)) + 1;
-    for (int l = h; l >= 1; --l) {
-        int c = 0;
-        if (sizeof(KT) == 4) {
-            NodeF nd;
-            nd.load(base + ((size_t)(off + k) << 5));
-            c = count_node<Upper>(nd.v, K, x);
-        } else {
-            const uint4 *p = reinterpret_cast<const uint4 *>(base + ((size_t)(off + k) << 5));
-            uint4 a = __ldg(p), b = __ldg(p + 1);
-            uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float lo = dequantise(w[q] & 0xffffu, X, m.invQ);
-                float hi = dequantise(w[q] >> 16, X, m.invQ);
-                c += Upper ? ((lo <= x) + (hi <= x)) : ((lo < x) + (hi < x));
-            }
-        }
-        // The root has cnt[h-1] real children, its other separators are +inf
-        // padding; when every real child's maximum is <= x (or < x) there is
-        // no answer in the bin.  Below the root the parent's choice
-        // guarantees a real child whose maximum exceeds x.
-        if (l == h && c >= (int)(((L0 - 1) >> (LK * (h - 1))) + 1)) {
-            r.idx = (int)n;
-            r.prev = bin_key<KT>(m, bi, internal, (int)n - 1, X);
-            return r;
-        }
-        off += ((L0 - 1) >> (LK * l)) + 1;
-        k = k * K + c;
-    }
-    // leaf
-    int c = 0;
-    float at = kInf, prev = -kInf;
-    if (sizeof(KT) == 4) {
-        NodeF nd;
-        nd.load(base + ((size_t)(off + k) << 5));
-        c = count_node<Upper>(nd.v, K, x);
-        at = pick8(nd.v, c < 8 ? c : 7);
-        prev = pick8(nd.v, c > 0 ? c - 1 : 0);
-    } else {
-        const uint4 *p = reinterpret_cast<const uint4 *>(base + ((size_t)(off + k) << 5));
-        uint4 a = __ldg(p), b = __ldg(p + 1);
-        uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        float vals[16];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            vals[2 * q] = dequantise(w[q] & 0xffffu, X, m.invQ);
-            vals[2 * q + 1] = dequantise(w[q] >> 16, X, m.invQ);
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) c += Upper ? (vals[q] <= x) : (vals[q] < x);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            at = (q == c) ? vals[q] : at;
-            prev = (q == c - 1) ? vals[q] : prev;
-        }
-    }
-    r.idx = (int)(k * K) + c;
-    if (r.idx >= (int)n) {
+    const int h = run_levels(L0, LK, R);
+    const char *run = reinterpret_cast<const char *>(m.store) + ((size_t)off << 5);
+    if (c >= (int)level_count(L0, LK, h)) {  // every key is below the query
         r.idx = (int)n;
-        r.at = kInf;
-    } else {
-        r.at = at;
+        r.prev = load_key<KT>(m, run + ((size_t)internal_nodes(n, LK, R) << 5), (int64_t)n - 1, X);
+        return r;
     }
-    if (r.idx > 0) r.prev = (c > 0) ? prev : bin_key<KT>(m, bi, internal, r.idx - 1, X);
+    uint32_t loff = 0, k = (uint32_t)c;
+    for (int l = h; l >= 1; --l) {
+        ld_node(run + ((size_t)(loff + k) << 5), pol, w);
+        const int cc = count_below<KT, Upper>(w, 0, cmp);
+        loff += level_count(L0, LK, l);
+        // cc < K below the root for any in-map query; the clamp only keeps a
+        // stray comparison inside the level
+        const uint32_t below = level_count(L0, LK, l - 1);
+        k = min(k * K + (uint32_t)cc, below - 1);
+    }
+    // leaf (loff is now the number of internal nodes)
+    const char *leaf = run + ((size_t)(loff + k) << 5);
+    ld_node(leaf, w);
+    c = count_below<KT, Upper>(w, 0, cmp);
+    r.idx = min((int)(k * K) + c, (int)n);
+    const int cl = r.idx - (int)(k * K);  // index inside this leaf (may be -1 .. K)
+    if (r.idx < (int)n) r.at = load_key<KT>(m, leaf, cl, X);
+    if (r.idx > 0) r.prev = load_key<KT>(m, leaf, cl - 1, X);
     return r;
 }
 
 // Branch-free binary search of the bin's sorted leaf run (same answers).
 template <typename KT, bool Upper>
-__device__ __forceinline__ SearchResult binary_search(const MapView &m, const uint2 &bi, float x,
-                                                      float X)
+__device__ __forceinline__ SearchResult binary_search(const MapView &m, uint32_t g, float x, float X, int &kb)
 {
-    constexpr int LK = KeyT<KT>::LK;
     SearchResult r;
-    const int n = (int)bi.y;
     r.idx = 0;
     r.at = kInf;
     r.prev = -kInf;
+    const uint2 on = __ldg(reinterpret_cast<const uint2 *>(m.hdr + g));
+    const uint32_t off = on.x;
+    const int n = (int)on.y;
+    kb = n;
     if (n == 0) return r;
-    const uint32_t internal = internal_nodes(bi.y, LK);
     int base = 0, len = n;
     while (len > 1) {
         int half = len >> 1;
-        float v = bin_key<KT>(m, bi, internal, base + half - 1, X);
+        float v = bin_key<KT>(m, off, n, base + half - 1, X);
         base = (Upper ? (v <= x) : (v < x)) ? base + half : base;
         len -= half;
     }
-    float v = bin_key<KT>(m, bi, internal, base, X);
+    float v = bin_key<KT>(m, off, n, base, X);
     int idx = base + (Upper ? (v <= x) : (v < x));
     r.idx = idx;
-    if (idx < n) r.at = (idx == base) ? v : bin_key<KT>(m, bi, internal, idx, X);
-    if (idx > 0) r.prev = (idx - 1 == base) ? v : bin_key<KT>(m, bi, internal, idx - 1, X);
+    if (idx < n) r.at = (idx == base) ? v : bin_key<KT>(m, off, n, idx, X);
+    if (idx > 0) r.prev = (idx - 1 == base) ? v : bin_key<KT>(m, off, n, idx - 1, X);
     return r;
 }
 
-template <typename KT, bool Upper>
-__device__ __forceinline__ SearchResult bin_search(const MapView &m, const uint2 &bi, float x, float X)
+// The search layout is a template parameter (SEARCH = CDDT_SEARCH_*), so a
+// kernel carries the code of one layout only.
+template <typename KT, bool Upper, int SEARCH>
+__device__ __forceinline__ SearchResult bin_search(const MapView &m, uint32_t g, float x, float X, uint64_t pol,
+                                                   int &kb)
 {
-    if (m.search == CDDT_SEARCH_BINARY) return binary_search<KT, Upper>(m, bi, x, X);
-    return tree_search<KT, Upper>(m, bi, x, X);
+    if (SEARCH == CDDT_SEARCH_BINARY) return binary_search<KT, Upper>(m, g, x, X, kb);
+    return tree_search<KT, Upper>(m, g, x, X, pol, kb);
 }
 
 // ------------------------------------------------------------ one ray cast
 
 // Result of casting one beam: range and its derivative direction.
 struct Cast {
-    float r;       // clamped range
+    float r;         // clamped range
     float dzx, dzy;  // d r / d(x, y): -(c, s) forward, +(c, s) backward, 0 if clamped / miss
-    int kb;        // bin size searched (-1: none)
+    int kb;          // bin size searched (-1: none)
 };
 
 // Cast from an in-map free cell position (pre-check already passed) in
 // direction k.  One search; if `pair` is set, the opposite direction k + N/2
 // is answered from the same search (Section IV-C: index i - 1).
-template <typename KT>
-__device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, int k, bool pair,
+template <typename KT, int SEARCH>
+__device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, int k, bool pair, uint64_t pol,
                                           Cast &fwd_out, Cast &bwd_out, bool &k_is_fwd)
 {
     const int S = m.S;
@@ -378,11 +464,8 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     const int s = bwd ? k - S : k;
     k_is_fwd = !bwd;
     const float4 sa = __ldg(reinterpret_cast<const float4 *>(m.slices + s));
-    const float4 sb = __ldg(reinterpret_cast<const float4 *>(m.slices + s) + 1);
     const float c = sa.x, sn = sa.y;
     const int T = __float_as_int(sa.z), nb = __float_as_int(sa.w);
-    const uint32_t sbase = __float_as_uint(sb.x);
-    const float X = sb.y;
     float xr, yr;
     project(x, y, c, sn, xr, yr);
     const int b = query_bin(yr, T);
@@ -391,12 +474,14 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     f.dzx = f.dzy = r.dzx = r.dzy = 0.0f;
     f.kb = r.kb = -1;
     if (b >= 0 && b < nb) {
-        const uint2 bi = __ldg(m.bins + sbase + b);
-        f.kb = r.kb = (int)bi.y;
+        const float2 sb = __ldg(reinterpret_cast<const float2 *>(m.slices + s) + 2);
+        const uint32_t g = __float_as_uint(sb.x) + (uint32_t)b;
+        const float X = sb.y;
+        int kb;
         if (!bwd || pair) {
             // forward: first key > x' (upper bound)
-            SearchResult sr = bin_search<KT, true>(m, bi, xr, X);
-            if (sr.idx < (int)bi.y) {
+            SearchResult sr = bin_search<KT, true, SEARCH>(m, g, xr, X, pol, kb);
+            if (sr.idx < kb) {
                 float d = __fsub_rn(sr.at, xr);
                 if (d < m.max_range) { f.r = d; f.dzx = -c; f.dzy = -sn; }
             }
@@ -405,10 +490,10 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
                 float pv = sr.prev;
                 int j = sr.idx - 1;
                 if (j >= 0 && pv == xr) {
-                    const uint32_t internal = internal_nodes(bi.y, KeyT<KT>::LK);
+                    const uint2 on = __ldg(reinterpret_cast<const uint2 *>(m.hdr + g));
                     while (j >= 0 && pv == xr) {
                         --j;
-                        if (j >= 0) pv = bin_key<KT>(m, bi, internal, j, X);
+                        if (j >= 0) pv = bin_key<KT>(m, on.x, on.y, j, X);
                     }
                 }
                 if (j >= 0) {
@@ -418,12 +503,13 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
             }
         } else {
             // backward only: last key < x' = (first key >= x') - 1
-            SearchResult sr = bin_search<KT, false>(m, bi, xr, X);
+            SearchResult sr = bin_search<KT, false, SEARCH>(m, g, xr, X, pol, kb);
             if (sr.idx > 0) {
                 float d = __fsub_rn(xr, sr.prev);
                 if (d < m.max_range) { r.r = d; r.dzx = c; r.dzy = sn; }
             }
         }
+        f.kb = r.kb = kb;
     }
     fwd_out = f;
     bwd_out = r;
@@ -497,10 +583,11 @@ __device__ __forceinline__ float beam_logp(const BeamConsts &m, const BeamObs &o
     float p_short = 0.0f, dshort = 0.0f;
     if (zs > 0.0f && o.z <= zs) {
         float den = -expm1f(-m.lam * zs);
-        p_short = o.e_lz / den;
+        float inv = __fdividef(1.0f, den);
+        p_short = o.e_lz * inv;
         if (Grad && o.z < zs) {
             float e = expf(-m.lam * zs);
-            dshort = -m.lam * o.e_lz * e / (den * den);
+            dshort = -m.lam * o.e_lz * e * inv * inv;
         }
     }
     const float p = m.z_hit * p_hit + m.z_short * p_short + o.c_mr;
@@ -521,6 +608,7 @@ struct cddt_s {
     float Q = 1, invQ = 1;
     int32_t pruned = 0;
     int32_t search = CDDT_SEARCH_TREE;
+    uint64_t generation = 0;  // bumped whenever the store, its layout or the search changes
     int64_t total_bins = 0;
     int64_t n_zp = 0;          // zero points (host copy, exact after each sync point)
     int64_t n_edge = 0;
@@ -530,7 +618,7 @@ struct cddt_s {
     float build_ms = 0, prune_ms = 0, update_ms = 0;
     // device buffers owned by the handle
     cddt::SliceInfo *slices = nullptr;
-    uint2 *bins = nullptr;
+    cddt::BinHdr *hdr = nullptr;
     void *store = nullptr;
     uint8_t *grid = nullptr;
     uint8_t *edge = nullptr;
@@ -547,7 +635,7 @@ struct cddt_s {
     {
         cddt::MapView v;
         v.slices = slices;
-        v.bins = bins;
+        v.hdr = hdr;
         v.store = store;
         v.grid = grid;
         v.W = W;

@@ -37,6 +37,56 @@ struct SensorArgs {
 cddt_status launch_sensor(const cddt_s *h, const SensorArgs &a, int mode, cudaStream_t st);
 cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int sorted, cudaStream_t st);
 
+// A device buffer freed on scope exit.
+struct Buf {
+    void *p = nullptr;
+    ~Buf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+    template <typename T> T *as() { return reinterpret_cast<T *>(p); }
+};
+
+template <typename KT> __device__ __forceinline__ KT pad_key();
+template <> __device__ __forceinline__ float pad_key<float>() { return kInf; }
+template <> __device__ __forceinline__ uint16_t pad_key<uint16_t>() { return 0xffffu; }
+
+// First key of a bin's leaf run.
+template <typename KT>
+__device__ __forceinline__ KT *leaf_run(void *store, uint32_t off, uint32_t n)
+{
+    constexpr int LK = KeyT<KT>::LK;
+    return reinterpret_cast<KT *>(store) + ((size_t)(off + internal_nodes(n, LK, KeyT<KT>::R)) << LK);
+}
+
+// The segments of a segmented sort: the leaf runs of a store's bins (hdr
+// set), or plain ranges base[off[id] .. off[id] + len[id]).
+template <typename KT>
+struct Segs {
+    void *store;
+    const BinHdr *hdr;
+    KT *base;
+    const uint32_t *off;
+    const uint32_t *len;
+    __device__ __forceinline__ void get(uint32_t id, KT *&p, uint32_t &n) const
+    {
+        if (hdr) {
+            n = hdr[id].n;
+            p = leaf_run<KT>(store, hdr[id].off, n);
+        } else {
+            n = len[id];
+            p = base + off[id];
+        }
+    }
+};
+
+// Sort every segment ascending (cddt_build.cu).  Synchronises `st`.
+template <typename KT>
+cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st);
+// Fill the trees and headers of every bin from the sorted leaf runs.
+cddt_status index_store(cddt_s *h, cudaStream_t st);
+// Slice tables' eps for pruning: 32 units in the last place of the largest
+// projected coordinate.
+float prune_eps(int W, int H);
+
 inline unsigned grid_cap(int64_t n, int threads, int64_t cap = 152 * 64)
 {
     int64_t b = (n + threads - 1) / threads;

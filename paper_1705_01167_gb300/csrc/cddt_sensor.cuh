@@ -1,0 +1,324 @@
+// cddt_sensor.cuh -- device code of the fused sensor model (Section VI):
+// per-particle traversal slots, the single-filter kernel and the persistent
+// batched kernel.  Included by the sensor and batched translation units,
+// which instantiate the kernels, and by cddt_query.cu for the shared types.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "cddt_internal.cuh"
+#include "cddt_kernels.cuh"
+
+namespace cddt {
+
+enum { MODE_FWD = 0, MODE_BWD = 1, MODE_FWDBWD = 2, MODE_WORK = 3 };
+
+// Work figures of one particle's traversal slot (MODE_WORK).
+struct WorkAcc {
+    unsigned long long trav = 0, beams = 0, nonempty = 0, probes = 0, paired = 0;
+};
+
+__device__ __forceinline__ int ceil_log2p1(int kb)
+{
+    // ceil(log2(kb + 1)) for kb >= 0
+    return kb <= 0 ? 0 : 32 - __clz((unsigned)kb);
+}
+
+// One particle's beams in traversal slots t = lane, lane + TPP, ... ; smem
+// holds phi[B], z[B], e_lz[B], c_mr[B].
+template <typename KT, int MODE, int SEARCH>
+__device__ __forceinline__ void particle_slots(const MapView &m, const SensorArgs &a, const float *sh,
+                                               int64_t p, bool valid, int lane, int TPP, uint64_t pol,
+                                               float &acc, float &gx, float &gy, WorkAcc &w, bool &ok_out)
+{
+    const int B = a.B, D = a.D;
+    const int T = D > 0 ? D : B;
+    float x = 0.f, y = 0.f, th = 0.f;
+    if (valid) {
+        x = __ldg(a.part + 3 * p);
+        y = __ldg(a.part + 3 * p + 1);
+        th = __ldg(a.part + 3 * p + 2);
+    }
+    const bool ok = valid && free_cell(m.grid, m.W, m.H, x, y);
+    ok_out = ok;
+    const float *phi = sh, *zz = sh + B, *elz = sh + 2 * B, *cmr = sh + 3 * B;
+    for (int t = lane; t < T; t += TPP) {
+        const int i = t;
+        const int j = (D > 0 && t + D < B) ? t + D : -1;
+        Cast ci, cj;
+        ci.r = cj.r = 0.0f;
+        ci.dzx = ci.dzy = cj.dzx = cj.dzy = 0.0f;
+        ci.kb = cj.kb = -1;
+        bool pairdone = false;
+        if (ok) {
+            int ki = 0, kj = 0;
+            bool vi = query_dir(__fadd_rn(th, phi[i]), m.inv_step, m.N, ki);
+            bool vj = j >= 0 && query_dir(__fadd_rn(th, phi[j]), m.inv_step, m.N, kj);
+            int kopp = ki + m.S;
+            kopp -= (kopp >= m.N) ? m.N : 0;
+            if (vj && vi && kj == kopp) {
+                Cast f, b;
+                bool kf;
+                cast_pair<KT, SEARCH>(m, x, y, ki, true, pol, f, b, kf);
+                ci = kf ? f : b;
+                cj = kf ? b : f;
+                pairdone = true;
+            } else {
+                if (vi) {
+                    Cast f, b;
+                    bool kf;
+                    cast_pair<KT, SEARCH>(m, x, y, ki, false, pol, f, b, kf);
+                    ci = kf ? f : b;
+                }
+                if (vj) {
+                    Cast f, b;
+                    bool kf;
+                    cast_pair<KT, SEARCH>(m, x, y, kj, false, pol, f, b, kf);
+                    cj = kf ? f : b;
+                }
+            }
+        }
+        if (MODE == MODE_WORK) {
+            if (ci.kb >= 0) {
+                w.beams++;
+                w.trav++;
+                w.nonempty += ci.kb > 0;
+                w.probes += ceil_log2p1(ci.kb);
+            }
+            if (j >= 0 && cj.kb >= 0) {
+                w.beams++;
+                if (pairdone) w.paired++;
+                else {
+                    w.trav++;
+                    w.nonempty += cj.kb > 0;
+                    w.probes += ceil_log2p1(cj.kb);
+                }
+            }
+            continue;
+        }
+        {
+            BeamObs o;
+            o.z = zz[i];
+            o.e_lz = elz[i];
+            o.c_mr = cmr[i];
+            float dl = 0.f;
+            float lp = beam_logp<MODE != MODE_FWD>(a.bc, o, ci.r, dl);
+            acc += lp;
+            if (MODE != MODE_FWD) { gx += dl * ci.dzx; gy += dl * ci.dzy; }
+            if (MODE == MODE_FWD && a.ranges && valid) a.ranges[p * B + i] = ci.r;
+        }
+        if (j >= 0) {
+            BeamObs o;
+            o.z = zz[j];
+            o.e_lz = elz[j];
+            o.c_mr = cmr[j];
+            float dl = 0.f;
+            float lp = beam_logp<MODE != MODE_FWD>(a.bc, o, cj.r, dl);
+            acc += lp;
+            if (MODE != MODE_FWD) { gx += dl * cj.dzx; gy += dl * cj.dzy; }
+            if (MODE == MODE_FWD && a.ranges && valid) a.ranges[p * B + j] = cj.r;
+        }
+    }
+}
+
+__device__ __forceinline__ void stage_beams(const SensorArgs &a, float *sh)
+{
+    for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
+        BeamObs o = beam_obs(a.bc, __ldg(a.obs + i));
+        sh[i] = __ldg(a.beam_off + i);
+        sh[a.B + i] = o.z;
+        sh[2 * a.B + i] = o.e_lz;
+        sh[3 * a.B + i] = o.c_mr;
+    }
+}
+
+template <int TPP>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void write_particle(const SensorArgs &a, int MODE, int64_t p, float acc, float gx,
+                                               float gy)
+{
+    if (MODE == MODE_FWD || MODE == MODE_FWDBWD) a.logw[p] = acc;
+    if (MODE == MODE_BWD) {
+        float gl = __ldg(a.grad_logw + p);
+        a.grad_xy[2 * p] = gl * gx;
+        a.grad_xy[2 * p + 1] = gl * gy;
+    }
+    if (MODE == MODE_FWDBWD) {
+        a.grad_xy[2 * p] = gx;
+        a.grad_xy[2 * p + 1] = gy;
+    }
+}
+
+template <typename KT, int MODE, int TPP, int SEARCH>
+__global__ void __launch_bounds__(256, 6) sensor_kernel(MapView m, SensorArgs a)
+{
+    extern __shared__ float sh[];
+    stage_beams(a, sh);
+    __syncthreads();
+    const uint64_t pol = policy_evict_last();
+    const int lane = threadIdx.x % TPP;
+    const int group = threadIdx.x / TPP;
+    const int ppb = blockDim.x / TPP;
+    WorkAcc w;
+    unsigned long long passed = 0;
+    for (int64_t pb = (int64_t)blockIdx.x * ppb; pb < a.P; pb += (int64_t)gridDim.x * ppb) {
+        const int64_t p = pb + group;
+        const bool valid = p < a.P;
+        float acc = 0.f, gx = 0.f, gy = 0.f;
+        bool ok;
+        particle_slots<KT, MODE, SEARCH>(m, a, sh, p, valid, lane, TPP, pol, acc, gx, gy, w, ok);
+        if (MODE == MODE_WORK) {
+            passed += (ok && lane == 0);
+            continue;
+        }
+        acc = group_sum<TPP>(acc);
+        if (MODE != MODE_FWD) {
+            gx = group_sum<TPP>(gx);
+            gy = group_sum<TPP>(gy);
+        }
+        if (lane == 0 && valid) write_particle(a, MODE, p, acc, gx, gy);
+    }
+    if (MODE == MODE_WORK) {
+        unsigned long long v[6] = {w.trav, w.beams, w.nonempty, w.probes, w.paired, passed};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            unsigned long long s = v[q];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if ((threadIdx.x & 31) == 0 && s) atomicAdd(a.work + q, s);
+        }
+    }
+}
+
+// ------------------------------------------------------------ batched
+
+struct __align__(16) FilterDev {
+    MapView m;
+    SensorArgs a;
+    int32_t key_u16;
+    int32_t pad[3];
+};
+
+struct WorkItem {
+    int32_t filter;
+    int32_t count;
+    int64_t first;
+};
+
+// Persistent batched sensor model: blocks take (filter, particle range)
+// items from an atomic queue until it is empty.  No block waits on another.
+// WARPS caps registers so that WARPS warps stay resident per SM (32 leaves
+// the compiler its natural 64 registers; 48 trades a few spills for
+// occupancy).  One launch serves the filters of one key type (a contiguous
+// item range).
+template <typename KT, int SEARCH, int TPP, int BLOCK, int WARPS>
+__global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
+    batched_kernel(const FilterDev *filters, const WorkItem *items, int64_t n_items,
+                   unsigned long long *queue, int32_t max_B)
+{
+    extern __shared__ float sh[];
+    __shared__ long long cur;
+    // the current item's filter descriptor, read by every thread from shared
+    // memory (uniform loads) instead of being held in registers
+    __shared__ __align__(16) FilterDev F;
+    const uint64_t pol = policy_evict_last();
+    const int lane = threadIdx.x % TPP;
+    const int group = threadIdx.x / TPP;
+    const int ppb = blockDim.x / TPP;
+    constexpr int kWords = (int)(sizeof(FilterDev) / sizeof(int4));
+    static_assert(sizeof(FilterDev) % sizeof(int4) == 0, "FilterDev must be a multiple of 16 bytes");
+    for (;;) {
+        if (threadIdx.x == 0) cur = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const long long it = cur;
+        if (it >= n_items) break;
+        const WorkItem wi = items[it];
+        for (int q = threadIdx.x; q < kWords; q += blockDim.x)
+            reinterpret_cast<int4 *>(&F)[q] = reinterpret_cast<const int4 *>(filters + wi.filter)[q];
+        __syncthreads();
+        stage_beams(F.a, sh);
+        __syncthreads();
+        WorkAcc w;
+        for (int64_t pb = wi.first; pb < wi.first + wi.count; pb += ppb) {
+            const int64_t p = pb + group;
+            const bool valid = p < wi.first + wi.count;
+            float acc = 0.f, gx = 0.f, gy = 0.f;
+            bool ok;
+            particle_slots<KT, MODE_FWD, SEARCH>(F.m, F.a, sh, p, valid, lane, TPP, pol, acc, gx, gy, w, ok);
+            acc = group_sum<TPP>(acc);
+            if (lane == 0 && valid) F.a.logw[p] = acc;
+        }
+        __syncthreads();
+    }
+    (void)max_B;
+}
+
+inline size_t beam_smem(int B) { return sizeof(float) * 4 * (size_t)B; }
+
+typedef void (*BatchedFn)(const FilterDev *, const WorkItem *, int64_t, unsigned long long *, int32_t);
+
+// Kernel pointer of the batched kernel for a key type and launch shape
+// (cddt_batched_f32.cu, cddt_batched_u16.cu); nullptr for an unknown shape.
+BatchedFn batched_fn_f32(int search, int tpp, int block, int regcap);
+BatchedFn batched_fn_u16(int search, int tpp, int block, int regcap);
+
+// Single-filter sensor launches (cddt_sensor_f32.cu, cddt_sensor_u16.cu).
+// Tree layout, every mode; the binary-search layout for the forward mode only
+// (it gives the same answers, so the other modes always use the tree).
+cddt_status launch_sensor_f32(const cddt_s *h, const SensorArgs &a, int mode, int tpp, int threads, cudaStream_t st);
+cddt_status launch_sensor_u16(const cddt_s *h, const SensorArgs &a, int mode, int tpp, int threads, cudaStream_t st);
+cddt_status launch_sensor_binary(const cddt_s *h, const SensorArgs &a, int tpp, int threads, cudaStream_t st);
+
+template <typename KT, int MODE, int SEARCH>
+inline cddt_status launch_sensor_tpp(const cddt_s *h, const SensorArgs &a, int tpp, int threads, cudaStream_t st)
+{
+    MapView m = h->view();
+    int ppb = threads / tpp;
+    int64_t blocks = (a.P + ppb - 1) / ppb;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    size_t sm = beam_smem(a.B);
+    void (*fn)(MapView, SensorArgs) = nullptr;
+    switch (tpp) {
+    case 1: fn = sensor_kernel<KT, MODE, 1, SEARCH>; break;
+    case 2: fn = sensor_kernel<KT, MODE, 2, SEARCH>; break;
+    case 4: fn = sensor_kernel<KT, MODE, 4, SEARCH>; break;
+    case 8: fn = sensor_kernel<KT, MODE, 8, SEARCH>; break;
+    case 16: fn = sensor_kernel<KT, MODE, 16, SEARCH>; break;
+    default: fn = sensor_kernel<KT, MODE, 32, SEARCH>; break;
+    }
+    if (sm > 48 * 1024) CDDT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    fn<<<(unsigned)blocks, threads, sm, st>>>(m, a);
+    CDDT_CUDA(cudaGetLastError());
+    return CDDT_OK;
+}
+
+template <typename KT>
+inline cddt_status launch_sensor_mode(const cddt_s *h, const SensorArgs &a, int mode, int tpp, int threads,
+                                      cudaStream_t st)
+{
+    switch (mode) {
+    case MODE_FWD: return launch_sensor_tpp<KT, MODE_FWD, CDDT_SEARCH_TREE>(h, a, tpp, threads, st);
+    case MODE_BWD: return launch_sensor_tpp<KT, MODE_BWD, CDDT_SEARCH_TREE>(h, a, tpp, threads, st);
+    case MODE_FWDBWD: return launch_sensor_tpp<KT, MODE_FWDBWD, CDDT_SEARCH_TREE>(h, a, tpp, threads, st);
+    default: return launch_sensor_tpp<KT, MODE_WORK, CDDT_SEARCH_TREE>(h, a, tpp, threads, st);
+    }
+}
+
+template <typename KT, int SEARCH, int WARPS>
+inline BatchedFn batched_fn_kt(int tpp, int block)
+{
+#define CDDT_BF(T, B) if (tpp == T && block == B) return batched_kernel<KT, SEARCH, T, B, WARPS>;
+    CDDT_BF(1, 256) CDDT_BF(1, 512)
+    CDDT_BF(2, 256) CDDT_BF(2, 512)
+    CDDT_BF(4, 256) CDDT_BF(4, 512)
+    CDDT_BF(8, 256) CDDT_BF(8, 512)
+#undef CDDT_BF
+    return nullptr;
+}
+
+}  // namespace cddt

@@ -1,0 +1,128 @@
+"""The persistent batched launch (many maps and filters of uneven sizes in one
+launch, optionally replayed as a CUDA graph) against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_01167_gb300 import synth
+from tests import gpu_cases as gc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_01167_gb300 import cddt
+    cddt.load()
+    return cddt
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _close(got, want, rtol=1e-5):
+    got = np.asarray(got, np.float64)
+    assert np.all(np.abs(got - want) <= rtol * np.maximum(1.0, np.abs(want))), (got[:4], want[:4])
+
+
+@pytest.fixture(scope="module")
+def batch(G, oracle):
+    """Maps of different sizes, theta discretisations and key types, each
+    with one or more filters of different particle counts and scans."""
+    specs = [  # (generator, W, H, N, max_range, u16, [(P, B), ...])
+        ("rect", 256, 256, 108, 300.0, False, [(1000, 61), (33, 61), (1, 7)]),
+        ("corr", 512, 384, 120, 400.0, False, [(2500, 61), (517, 1081)]),
+        ("corr", 320, 320, 64, 250.0, True, [(700, 61), (5, 2)]),
+        ("rect", 64, 64, 16, 80.0, False, [(0, 61), (64, 61)]),
+    ]
+    maps, filters, refs = [], [], []
+    for mi, (kind, W, H, N, mr, u16, fl) in enumerate(specs):
+        g = synth.rect_map(W, H, seed=900 + mi) if kind == "rect" else synth.corridor_map(W, H, seed=900 + mi, r_min=48)
+        d = G.CDDT(dev(g), N, mr, u16=u16)
+        o = oracle.OracleCDDT(g, N, mr, u16=u16)
+        maps.append((d, o))
+        for fi, (P, B) in enumerate(fl):
+            bo = synth.beam_offsets(B)
+            D = synth.pair_offset(B)
+            gt = synth.uniform_particles(g, 1, seed=1000 + 10 * mi + fi)[0]
+            obs = gc.observations(o, gt, bo, mr, seed=2000 + 10 * mi + fi)
+            parts = synth.tracking_particles(gt.astype(np.float64), P, seed=3000 + 10 * mi + fi) if P else np.zeros((0, 3), np.float32)
+            m = G.beam_model(mr)
+            f = dict(map=d, particles=dev(parts).reshape(-1, 3), beam_off=dev(bo), obs=dev(obs), model=m,
+                     logw=torch.full((max(P, 1),), float("nan"), device="cuda")[:P], pair_offset=D)
+            filters.append(f)
+            want = o.sensor_weights(parts, bo, obs, oracle.beam_model(mr), nthreads=8) if P else np.zeros(0)
+            refs.append(want)
+    return maps, filters, refs
+
+
+def _check(filters, refs):
+    torch.cuda.synchronize()
+    for f, want in zip(filters, refs):
+        _close(f["logw"].cpu().numpy(), want)
+
+
+def test_plan_run_matches_oracle(G, batch):
+    maps, filters, refs = batch
+    plan = G.Plan(filters)
+    assert plan.items > len([f for f in filters if f["particles"].shape[0]])
+    for tpp in (1, 2, 4, 8):
+        for block in (256, 512):
+            for regcap in (0, 1):
+                for f in filters:
+                    f["logw"].fill_(float("nan"))
+                plan.set_shape(tpp, block // tpp * 2 if tpp < 8 else 64, block, regcap)
+                plan.run()
+                _check(filters, refs)
+    plan.close()
+
+
+def test_plan_autotune_and_graph(G, batch):
+    maps, filters, refs = batch
+    plan = G.Plan(filters)
+    shape = plan.autotune()
+    assert shape["tpp"] in (1, 2, 4, 8)
+    for f in filters:
+        f["logw"].fill_(float("nan"))
+    plan.launch_graph()
+    _check(filters, refs)
+    for f in filters:
+        f["logw"].fill_(float("nan"))
+    plan.launch_graph()  # replay
+    _check(filters, refs)
+    plan.close()
+
+
+def test_plan_follows_handle_changes(G, batch):
+    """A plan re-reads its handles after a change (here the search layout),
+    so later runs use the current store."""
+    maps, filters, refs = batch
+    plan = G.Plan(filters)
+    plan.run()
+    _check(filters, refs)
+    for d, _ in maps:
+        d.set_search(G.SEARCH_BINARY)
+    for f in filters:
+        f["logw"].fill_(float("nan"))
+    plan.run()
+    _check(filters, refs)
+    for f in filters:
+        f["logw"].fill_(float("nan"))
+    plan.launch_graph()
+    _check(filters, refs)
+    for d, _ in maps:
+        d.set_search(G.SEARCH_TREE)
+    plan.close()
+
+
+def test_plan_argument_errors(G, batch):
+    maps, filters, refs = batch
+    plan = G.Plan(filters[:2])
+    with pytest.raises(G.CDDTError):
+        plan.set_shape(3, 64, 256)
+    with pytest.raises(G.CDDTError):
+        plan.set_shape(1, 64, 300)
+    plan.close()
