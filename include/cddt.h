@@ -138,6 +138,31 @@ CDDT_API cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const ui
 CDDT_API cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
                                  int32_t sort_by_slice, void *stream);
 
+/* Slice-sorted ray casting that allocates no device memory.  The paper has
+ * no counterpart: this entry point serves callers that cannot call
+ * cudaMalloc while they run -- an application that reserves all device
+ * memory up front and gives libraries fixed budgets, or a real-time loop that
+ * forbids allocation after start-up.  It returns the same ranges as
+ * cddt_calc_range_many(h, pose_dev, range_dev, n, 1, stream), but keeps its
+ * scratch in one fixed buffer of about 7.3 MB that is part of the library's
+ * device image (held on every device that loads the library until the
+ * process exits) instead of memory the handle allocates.
+ *   n            0 .. CDDT_NOALLOC_MAX_QUERIES queries (float [n][3] poses,
+ *                float [n] ranges, device memory owned by the caller).
+ *   theta_disc   of the handle at most CDDT_NOALLOC_MAX_THETA_DISC.
+ * Larger inputs return CDDT_ERR_ARG without launching anything.
+ * The first call on a device looks up the buffer's device address (a
+ * one-time set-up per device, under a lock); make that first call before any
+ * stream capture.  Every call shares the one buffer, which keeps the last
+ * call's contents (nothing in it needs to start at zero): calls whose GPU
+ * work overlaps -- on different streams, or from different threads -- race
+ * on it, so the caller must order them.  The call calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Errors: ARG, CUDA. */
+#define CDDT_NOALLOC_MAX_QUERIES 262144
+#define CDDT_NOALLOC_MAX_THETA_DISC 2048
+CDDT_API cddt_status cddt_calc_range_many_noalloc(cddt_t h, const float *pose_dev, float *range_dev,
+                                                  int64_t n, void *stream);
+
 /* Fused sensor model (Section VI): for every particle p, log w_p =
  * sum_i log p(obs_i | z*_i), z*_i the CDDT range from (x_p, y_p) at theta_p +
  * beam_off_i (one float32 add).

@@ -29,8 +29,10 @@ EXPORTED = (
     "cddt_plan_create", "cddt_plan_autotune", "cddt_plan_set_shape", "cddt_plan_get_shape",
     "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
-    "cddt_sensor_work", "cddt_status_string", "cddt_version",
+    "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc",
 )
+NOALLOC_MAX_QUERIES = 262144
+NOALLOC_MAX_THETA_DISC = 2048
 
 
 class CDDTError(RuntimeError):
@@ -93,6 +95,7 @@ def load(build_if_missing: bool = True):
             "cddt_prune": (st, [vp, vp]),
             "cddt_update_cells": (st, [vp, vp, vp, i32, vp]),
             "cddt_calc_range_many": (st, [vp, vp, vp, i64, i32, vp]),
+            "cddt_calc_range_many_noalloc": (st, [vp, vp, vp, i64, vp]),
             "cddt_sensor_weights": (st, [vp, vp, i64, vp, vp, i32, i32, C.POINTER(BeamModel), vp, vp, vp]),
             "cddt_sensor_weights_backward": (st, [vp, vp, i64, vp, vp, i32, i32, C.POINTER(BeamModel), vp, vp, vp]),
             "cddt_sensor_weights_fwd_bwd": (st, [vp, vp, i64, vp, vp, i32, i32, C.POINTER(BeamModel), vp, vp, vp]),
@@ -269,6 +272,19 @@ class CDDT:
             _check(load().cddt_calc_range_many(self._h, _ptr(poses), _ptr(out), n,
                                                int(bool(sort_by_slice)), _stream(stream)),
                    "cddt_calc_range_many")
+        return out
+
+    def calc_range_many_noalloc(self, poses: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """Slice-sorted ray casts into ``out`` with no device allocation (the
+        library's fixed scratch; at most NOALLOC_MAX_QUERIES queries)."""
+        _dev(poses, torch.float32, "poses")
+        _dev(out, torch.float32, "out")
+        n = poses.numel() // 3
+        if poses.numel() != 3 * n or out.numel() != n:
+            raise ValueError("poses must be [n, 3] and out [n]")
+        with torch.cuda.device(self.device):
+            _check(load().cddt_calc_range_many_noalloc(self._h, _ptr(poses), _ptr(out), n, _stream(stream)),
+                   "cddt_calc_range_many_noalloc")
         return out
 
     def _sensor_args(self, particles, beam_off, obs):

@@ -192,6 +192,62 @@ cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int 
     return CDDT_OK;
 }
 
+// Slice-sorted ray casting on caller-provided scratch (no allocation).  The
+// scratch layout is that of calc_range's sorted path; sorted_scratch_bytes
+// gives its size for n queries.
+int64_t sorted_scratch_bytes(const cddt_s *h, int64_t n)
+{
+    const int nbk = h->S + 1;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) return -1;
+    int64_t nblk = std::min<int64_t>((int64_t)nsm * 4, (n + kSortThreads - 1) / kSortThreads);
+    if (nblk < 1) nblk = 1;
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    nblk = std::max<int64_t>((n + chunk - 1) / std::max<int64_t>(chunk, 1), 1);
+    const int64_t ncount = (int64_t)nbk * nblk;
+    return 8 * (scan_scratch_elems(ncount) + 2) + 4 * ncount + 16 + 4 * n + 4 * n + 12 * n;
+}
+
+cddt_status calc_range_sorted_into(cddt_s *h, const float *pose, float *out, int64_t n, void *scratch,
+                                   int64_t scratch_bytes, cudaStream_t st)
+{
+    if (n == 0) return CDDT_OK;
+    MapView m = h->view();
+    const int threads = 256;
+    const int nbk = h->S + 1;
+    const size_t hs = sizeof(uint32_t) * nbk;
+    if (hs > 48 * 1024) return CDDT_ERR_ARG;
+    int nsm = 0;
+    CDDT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    int64_t nblk = std::min<int64_t>((int64_t)nsm * 4, (n + kSortThreads - 1) / kSortThreads);
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    nblk = (n + chunk - 1) / chunk;
+    const int64_t ncount = (int64_t)nbk * nblk;
+    if (sorted_scratch_bytes(h, n) > scratch_bytes) return CDDT_ERR_ARG;
+    char *p = reinterpret_cast<char *>(scratch);
+    uint64_t *scan_scratch = reinterpret_cast<uint64_t *>(p);
+    p += 8 * (scan_scratch_elems(ncount) + 2);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(p);
+    p += 4 * ncount;
+    p = reinterpret_cast<char *>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    uint32_t *bucket = reinterpret_cast<uint32_t *>(p);
+    p += 4 * n;
+    uint32_t *perm = reinterpret_cast<uint32_t *>(p);
+    p += 4 * n;
+    float *pose_sorted = reinterpret_cast<float *>(p);
+    bucket_count_kernel<<<(unsigned)nblk, kSortThreads, hs, st>>>(m, pose, n, chunk, bucket, counts, nbk);
+    exclusive_scan_u32(counts, counts, ncount, scan_scratch, scan_scratch + scan_scratch_elems(ncount), st);
+    place_kernel<<<(unsigned)nblk, kSortThreads, hs, st>>>(bucket, pose, n, chunk, counts, nbk, perm, pose_sorted);
+    const unsigned blocks = grid_cap(n, threads, 152 * 64);
+    const bool bin = h->search == CDDT_SEARCH_BINARY;
+    if (h->u16 && bin) calc_range_sorted_kernel<uint16_t, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
+    else if (h->u16) calc_range_sorted_kernel<uint16_t, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
+    else if (bin) calc_range_sorted_kernel<float, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
+    else calc_range_sorted_kernel<float, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
+    CDDT_CUDA(cudaGetLastError());
+    return CDDT_OK;
+}
+
 // ------------------------------------------------------------ plans
 
 }  // namespace cddt
