@@ -138,12 +138,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+# Device-code files that define each profiled kernel; a recorded ncu traffic
+# figure is reported only while these files are unchanged.
+KERNEL_SOURCES = {
+    "batched_kernel": ("cddt_internal.cuh", "cddt_sensor.cuh", "cddt_batched_f32.cu"),
+    "calc_range_kernel": ("cddt_internal.cuh", "cddt_query.cu"),
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1705_01167_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -154,7 +161,7 @@ def recorded_traffic(kernel: str, launch_units: int):
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
-    if not d or d.get("source_sha") != kernel_source_sha():
+    if not d or d.get("source_sha") != kernel_source_sha(kernel):
         return None
     return d["dram_bytes_per_unit"] * launch_units
 
@@ -457,7 +464,7 @@ def main():
     ap.add_argument("--shape-tpp", type=int, default=1)
     ap.add_argument("--shape-ppi", type=int, default=512)
     ap.add_argument("--shape-block", type=int, default=512)
-    ap.add_argument("--shape-regcap", type=int, default=0)
+    ap.add_argument("--shape-regcap", type=int, default=1)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)

@@ -252,8 +252,13 @@ CDDT_API cddt_status cddt_plan_run(cddt_plan p, void *stream);
  * the first call.  Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_plan_launch_graph(cddt_plan p, void *stream);
 
-/* Number of work items of the plan, and of filters. */
+/* Number of work items of the plan. */
 CDDT_API int64_t cddt_plan_items(cddt_plan p);
+
+/* Work items per kernel launch of the next run: items_per_group int64 [4] for
+ * (float32 keys, tree), (float32, binary search), (16-bit, tree), (16-bit,
+ * binary search), after regrouping for any handle change.  Errors: ARG. */
+CDDT_API cddt_status cddt_plan_groups(cddt_plan p, int64_t *items_per_group);
 
 CDDT_API cddt_status cddt_plan_destroy(cddt_plan p);
 

@@ -29,7 +29,7 @@ EXPORTED = (
     "cddt_plan_create", "cddt_plan_autotune", "cddt_plan_set_shape", "cddt_plan_get_shape",
     "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
-    "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc",
+    "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
             "cddt_plan_run": (st, [vp, vp]),
             "cddt_plan_launch_graph": (st, [vp, vp]),
             "cddt_plan_items": (i64, [vp]),
+            "cddt_plan_groups": (st, [vp, vp]),
             "cddt_plan_destroy": (st, [vp]),
             "cddt_set_search": (st, [vp, i32]),
             "cddt_get_stats": (st, [vp, C.POINTER(Stats)]),
@@ -417,6 +418,13 @@ class Plan:
     @property
     def items(self) -> int:
         return load().cddt_plan_items(self._h)
+
+    def groups(self):
+        """Work items per launch: (f32 tree, f32 binary, u16 tree, u16 binary)."""
+        import numpy as np
+        out = np.zeros(4, np.int64)
+        _check(load().cddt_plan_groups(self._h, out.ctypes.data_as(C.c_void_p)), "cddt_plan_groups")
+        return tuple(int(v) for v in out)
 
     def close(self):
         if getattr(self, "_h", None):

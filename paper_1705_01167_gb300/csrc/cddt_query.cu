@@ -375,8 +375,9 @@ cddt_status plan_create(const cddt_filter *filters, int32_t n, cudaStream_t st, 
 
 cddt_status plan_run(cddt_plan_s *p, cudaStream_t st)
 {
-    if (plan_stale(p)) {
+    if (plan_stale(p)) {  // new views, and items regrouped by key type and search layout
         cddt_status rc = plan_upload(p, st);
+        if (rc == CDDT_OK) rc = plan_items(p, st);
         if (rc != CDDT_OK) return rc;
     }
     if (p->built_ppi != p->ppi) {
@@ -411,6 +412,7 @@ cddt_status plan_launch_graph(cddt_plan_s *p, cudaStream_t st)
 {
     if (plan_stale(p)) {
         cddt_status rc = plan_upload(p, st);
+        if (rc == CDDT_OK) rc = plan_items(p, st);
         if (rc != CDDT_OK) return rc;
     }
     if (p->built_ppi != p->ppi) {
@@ -539,6 +541,13 @@ cddt_status cddt_plan_launch_graph(cddt_plan p, void *stream)
 }
 
 int64_t cddt_plan_items(cddt_plan p) { return p ? p->n_items : -1; }
+
+cddt_status cddt_plan_groups(cddt_plan p, int64_t *items_per_group)
+{
+    if (!p || !items_per_group) return CDDT_ERR_ARG;
+    for (int q = 0; q < 4; ++q) items_per_group[q] = p->group_start[q + 1] - p->group_start[q];
+    return CDDT_OK;
+}
 
 cddt_status cddt_plan_destroy(cddt_plan p)
 {

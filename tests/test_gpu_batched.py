@@ -103,12 +103,16 @@ def test_plan_follows_handle_changes(G, batch):
     plan = G.Plan(filters)
     plan.run()
     _check(filters, refs)
+    g0 = plan.groups()
+    assert g0[1] == 0 and g0[3] == 0 and g0[0] > 0 and g0[2] > 0
     for d, _ in maps:
         d.set_search(G.SEARCH_BINARY)
     for f in filters:
         f["logw"].fill_(float("nan"))
     plan.run()
     _check(filters, refs)
+    g1 = plan.groups()
+    assert g1[0] == 0 and g1[2] == 0 and g1[1] == g0[0] and g1[3] == g0[2]
     for f in filters:
         f["logw"].fill_(float("nan"))
     plan.launch_graph()
