@@ -300,6 +300,17 @@ def cell_toggles(grid: np.ndarray, n_insert: int, n_remove: int,
     return np.ascontiguousarray(xy[perm]), np.ascontiguousarray(occ[perm])
 
 
+def apply_writes(grid: np.ndarray, xy: np.ndarray, occ: np.ndarray) -> np.ndarray:
+    """The grid after cell writes applied in order (later writes to a cell
+    win); writes outside the map are skipped.  Returns a new array."""
+    g = grid.copy()
+    H, W = g.shape
+    for (x, y), v in zip(np.asarray(xy).tolist(), np.asarray(occ).tolist()):
+        if 0 <= x < W and 0 <= y < H:
+            g[y, x] = 1 if v else 0
+    return g
+
+
 # ---------------------------------------------------------------- workloads
 
 BEAM_MODEL_DEFAULT = dict(z_hit=0.75, z_short=0.01, z_max=0.07, z_rand=0.12,
