@@ -1,27 +1,39 @@
 """Benchmark: CDDT ray casts per second fused with the beam sensor model.
 
-Default workload (the 2000 x 2000 corridor configuration): a seeded
+Default workload (`--workload corridor2000`): a seeded 2000 x 2000
 recursive-division map (walls 1-3 cells, doors 3-20, ~8 % occupied),
 theta_disc = 200, max range 1000 cells.  A ground-truth pose random-walks for
 200 filter steps; each step has 2500 particles drawn around it and its own
 61-beam, 270-degree scan.  One benchmark step weights all 200 filter steps
 (500,000 particles x 61 beams = 30.5 M ray casts) in one persistent batched
-launch; the CDDT (about 290 MB with its search trees) is resident in HBM and
-L2 is flushed between steps.  Extra keys report the same work as 200
-per-filter launches, as a CUDA graph, on the pruned CDDT, and a 10 M-query
-calc_range_many sweep.
+launch; the CDDT (288 MB with its search trees) is resident in HBM and L2
+is flushed (a 256 MB write) between steps.  Extra keys report the same work
+as 200 per-filter launches, as a CUDA graph, with the binary-search layout,
+on the pruned CDDT, and a 10 M-query calc_range_many sweep.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {cddt,reference}]
+Other workloads (same JSON line, `config.name` names them):
+  rects256      256 x 256 rectangles, theta_disc 108: one 1000-particle filter
+  batched64     64 maps 512^2..4096^2, theta_disc 100..360, 500..10000
+                particles each: one persistent launch vs 64 per-filter launches
+  diff2000      forward + adjoint, 4096 x 61 and 1024 x 1081 beams, with 10
+                gradient refinement steps
+  update4000    4000 x 4000, theta_disc 360: 10^4 cell writes through
+                cddt_update_cells, then 100,000 particles x 61 beams
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl {cddt,reference}]
 
 `--impl reference` times the CPU oracle (the paper's plain CDDT: sorted
-bins, binary search) on the same workload on the host cores.
+bins, binary search, float64 beam model) on the default workload on the
+host cores.  Under torchrun every rank runs its own copy of the workload
+(particles drawn from a rank-dependent seed: weak scaling) and the step time
+is the maximum over ranks.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -34,40 +46,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from paper_1705_01167_gb300 import synth  # noqa: E402
+from paper_1705_01167_gb300 import synth, workloads as WL  # noqa: E402
 
 METRIC = "ray casts/s fused w/ sensor model on 1 GB300, % of L2/HBM gather roofline"
 UNIT = "ray casts/s"
-W_MAP = H_MAP = 2000
-THETA = 200
-MAX_RANGE = 1000.0
-STEPS = 200
-PARTICLES = 2500
-BEAMS = 61
-SWEEP = 10_000_000
-WORKLOAD = (f"corridor {W_MAP}x{H_MAP} (~8% occupied, walls 1-3, doors 3-20), theta_disc {THETA}, "
-            f"max range {MAX_RANGE:g}; {STEPS} filter steps x {PARTICLES} particles x {BEAMS} beams "
-            f"(270 deg) per benchmark step, one batched launch")
-
-
-# ------------------------------------------------------------------ inputs
-
-def make_workload():
-    """Seeded inputs of the corridor configuration (host arrays)."""
-    g = synth.corridor_map(W_MAP, H_MAP)
-    gt = synth.gt_walk(g, STEPS, seed=synth.SEED_PARTICLES)
-    parts = np.stack([synth.tracking_particles(gt[t], PARTICLES, seed=synth.SEED_PARTICLES + 1000 + t)
-                      for t in range(STEPS)])
-    bo = synth.beam_offsets(BEAMS)
-    D = synth.pair_offset(BEAMS)
-    noise = np.stack([synth.noise(BEAMS, 2.0, seed=synth.SEED_OBS + t) for t in range(STEPS)])
-    sweep = synth.uniform_queries(g, SWEEP, seed=synth.SEED_PARTICLES + 7)
-    return dict(grid=g, gt=gt, parts=parts.astype(np.float32), bo=bo, D=D, noise=noise, sweep=sweep)
-
-
-def gt_queries(gt, bo):
-    return np.concatenate([np.stack([np.full(bo.size, p[0]), np.full(bo.size, p[1]),
-                                     (np.float32(p[2]) + bo)], 1) for p in gt]).astype(np.float32)
+WORKLOAD_TEXT = {
+    "corridor2000": ("corridor 2000x2000 (~8% occupied, walls 1-3, doors 3-20), theta_disc 200, max range 1000; "
+                     "200 filter steps x 2500 particles x 61 beams (270 deg) per benchmark step, one batched launch"),
+    "rects256": "rectangles 256x256 (~17% occupied), theta_disc 108, max range 300; 1000 particles x 61 beams",
+    "batched64": ("64 corridor maps 512^2..4096^2, theta_disc 100..360, 500..10000 particles x 61 beams each; "
+                  "one persistent launch"),
+    "diff2000": ("corridor 2000x2000, theta_disc 200; forward + adjoint for 4096 x 61 and 1024 x 1081 beams, "
+                 "plus 10 gradient refinement steps"),
+    "update4000": ("corridor 4000x4000, theta_disc 360, max range 1000; 10^4 cell writes per step through "
+                   "cddt_update_cells, then 100,000 particles x 61 beams"),
+}
 
 
 # ------------------------------------------------------------------ clocks
@@ -128,7 +121,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ helpers
+# ------------------------------------------------------------------ roofline helpers
 
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -174,13 +167,21 @@ def algorithmic_bytes(work: dict, P: int) -> int:
     return 8 * work["traversals"] + 4 * work["probes"] + 4 * work["paired"] + 17 * P
 
 
-def dist_setup(n_gpus):
+def add_work(acc: dict, w: dict):
+    for k, v in w.items():
+        acc[k] = acc.get(k, 0) + v
+    return acc
+
+
+# ------------------------------------------------------------------ ranks
+
+def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        import torch.distributed as dist
         import torch
+        import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     return world, rank, local
@@ -202,224 +203,347 @@ def max_over_ranks(world, v: float) -> float:
     return float(t.item())
 
 
-# ------------------------------------------------------------------ oracle arm
+class Timer:
+    """Device time of a step with CUDA events on the launching stream, L2
+    flushed (a 256 MB write) before every step, barriers around the region."""
 
-def cpu_oracle_run(wl, steps, cores):
-    """The CPU oracle (sorted bins, binary search, float64 beam model) over
-    `steps` of the filter steps on `cores` host threads.  Returns (seconds,
-    ray casts)."""
-    from oracle import oracle as O
-    o = wl.get("_oracle")
-    if o is None:
-        o = O.OracleCDDT(wl["grid"], THETA, MAX_RANGE)
-        wl["_oracle"] = o
-    m = O.beam_model(MAX_RANGE)
-    obs = wl["obs"]
-    t0 = time.perf_counter()
-    for t in range(steps):
-        o.sensor_weights(wl["parts"][t], wl["bo"], obs[t], m, nthreads=cores)
-    return time.perf_counter() - t0, steps * PARTICLES * BEAMS
+    def __init__(self, world, dev):
+        import torch
+        self.torch = torch
+        self.world = world
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
-
-def oracle_obs(wl):
-    from oracle import oracle as O
-    o = O.OracleCDDT(wl["grid"], THETA, MAX_RANGE)
-    wl["_oracle"] = o
-    r = o.calc_range(gt_queries(wl["gt"], wl["bo"]), nthreads=os.cpu_count() or 1)
-    wl["obs"] = np.clip(r.reshape(STEPS, BEAMS) + wl["noise"], 0, MAX_RANGE).astype(np.float32)
-
-
-def run_reference(args):
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
-    if rank != 0:
-        return 0
-    cores = os.cpu_count() or 1
-    wl = make_workload()
-    oracle_obs(wl)
-    sample_steps = 40  # a bounded sample of the 200 filter steps per benchmark step
-    for _ in range(args.warmup):
-        cpu_oracle_run(wl, sample_steps, cores)
-    tot, rays = 0.0, 0
-    for _ in range(args.steps):
-        dt, r = cpu_oracle_run(wl, sample_steps, cores)
-        tot += dt
-        rays += r
-    value = rays / tot
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{sample_steps} of {STEPS} filter steps per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{sample_steps} filter steps x {PARTICLES} particles x {BEAMS} beams per step"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line))
-    return 0
-
-
-# ------------------------------------------------------------------ GPU arm
-
-def run_gpu(args):
-    import torch
-
-    world, rank, local = dist_setup(args.gpus)
-    from paper_1705_01167_gb300 import cddt as G
-    G.load()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-
-    wl = make_workload()
-    bo = wl["bo"]
-    D = wl["D"]
-    grid = torch.from_numpy(wl["grid"]).to(dev)
-    t0 = time.perf_counter()
-    d = G.CDDT(grid, THETA, MAX_RANGE)
-    torch.cuda.synchronize()
-    build_wall = time.perf_counter() - t0
-    st0 = d.stats()
-    # observations: cast from the ground truth pose of each step, plus noise
-    r = d.calc_range_many(torch.from_numpy(gt_queries(wl["gt"], bo)).to(dev)).cpu().numpy()
-    obs = np.clip(r.reshape(STEPS, BEAMS) + wl["noise"], 0, MAX_RANGE).astype(np.float32)
-    wl["obs"] = obs
-    parts_d = torch.from_numpy(wl["parts"].reshape(-1, 3)).to(dev).contiguous()
-    bo_d = torch.from_numpy(bo).to(dev)
-    obs_d = torch.from_numpy(obs).to(dev).contiguous()
-    logw_d = torch.empty(STEPS * PARTICLES, dtype=torch.float32, device=dev)
-    m = G.beam_model(MAX_RANGE)
-    P = PARTICLES
-
-    def filters_for(handle):
-        return [dict(map=handle, particles=parts_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t],
-                     model=m, logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(STEPS)]
-
-    plan = G.Plan(filters_for(d))
-    shape = plan.autotune()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def timed(fn, k, w):
+    def __call__(self, fn, k, w):
+        torch = self.torch
+        stream = torch.cuda.current_stream()
         for _ in range(w):
             fn()
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        barrier(world)
+        barrier(self.world)
         torch.cuda.synchronize()
         for i in range(k):
-            flush.fill_(float(i))
+            self.flush.fill_(float(i))
             ev[i][0].record(stream)
             fn()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-        barrier(world)
+        barrier(self.world)
         return [a.elapsed_time(b) for a, b in ev]
 
-    rays_per_step = STEPS * PARTICLES * BEAMS
-    with ClockSampler(local) as clk:
-        ms = timed(lambda: plan.run(), args.steps, args.warmup)
+
+def base_line(args, world, value, ms_step, workload, extra_config=None):
+    cfg = {"workload": WORKLOAD_TEXT[workload], "name": workload, "l2": "flushed between steps (256 MB write)",
+           "inputs": "resident in HBM"}
+    if extra_config:
+        cfg.update(extra_config)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg}
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def cpu_oracle_run(o, parts, bo, obs, steps, cores, max_range):
+    """The CPU oracle (sorted bins, binary search, float64 beam model) over
+    `steps` filter steps on `cores` host threads: (seconds, ray casts)."""
+    from oracle import oracle as O
+    m = O.beam_model(max_range)
+    t0 = time.perf_counter()
+    for t in range(steps):
+        o.sensor_weights(parts[t], bo, obs[t], m, nthreads=cores)
+    return time.perf_counter() - t0, steps * parts.shape[1] * bo.size
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    w = WL.corridor2000(sweep=0)
+    o = O.OracleCDDT(w["grid"], w["theta_disc"], w["max_range"])
+    r = o.calc_range(WL.gt_queries(w["gt"], w["beam_off"]), nthreads=cores).reshape(len(w["gt"]), -1)
+    obs = np.clip(r + w["noise"], 0, w["max_range"]).astype(np.float32)
+    sample = 40  # filter steps per benchmark step: a bounded sample of the 200
+    for _ in range(args.warmup):
+        cpu_oracle_run(o, w["parts"], w["beam_off"], obs, sample, cores, w["max_range"])
+    tot, rays = 0.0, 0
+    for _ in range(args.steps):
+        dt, n = cpu_oracle_run(o, w["parts"], w["beam_off"], obs, sample, cores, w["max_range"])
+        tot += dt
+        rays += n
+    value = rays / tot
+    line = base_line(args, 1, value, 1e3 * tot / args.steps, "corridor2000",
+                     {"sample": f"{sample} of 200 filter steps per benchmark step"})
+    line.update({"impl": "reference", "n_gpus": args.gpus,
+                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "sample": f"{sample} filter steps x 2500 particles x 61 beams per step"},
+                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU workloads
+
+def bench_corridor(args, G, torch, dev, world, rank):
+    w = WL.corridor2000(seed_offset=rank)
+    bo, D, mr = w["beam_off"], w["D"], w["max_range"]
+    S, P = w["parts"].shape[:2]
+    B = bo.size
+    grid = torch.from_numpy(w["grid"]).to(dev)
+    t0 = time.perf_counter()
+    d = G.CDDT(grid, w["theta_disc"], mr)
+    torch.cuda.synchronize()
+    build_wall = time.perf_counter() - t0
+    st0 = d.stats()
+    # observations: cast from each step's ground-truth pose, plus noise
+    r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], bo)).to(dev)).cpu().numpy()
+    obs = np.clip(r.reshape(S, B) + w["noise"], 0, mr).astype(np.float32)
+    parts_d = torch.from_numpy(w["parts"].reshape(-1, 3)).to(dev).contiguous()
+    bo_d = torch.from_numpy(bo).to(dev)
+    obs_d = torch.from_numpy(obs).to(dev).contiguous()
+    logw_d = torch.empty(S * P, dtype=torch.float32, device=dev)
+    m = G.beam_model(mr)
+
+    def filters_for(handle):
+        return [dict(map=handle, particles=parts_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t],
+                     model=m, logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(S)]
+
+    plan = G.Plan(filters_for(d))
+    shape = plan.autotune()
+    timed = Timer(world, dev)
+    rays_per_step = S * P * B
+    with ClockSampler(dev.index) as clk:
+        ms = timed(plan.run, args.steps, args.warmup)
     clocks = clk.summary()
-    ms_step = max_over_ranks(world, sum(ms) / len(ms))
+    ms_step = max_over_ranks(world, statistics.mean(ms))
     value = world * rays_per_step / (ms_step * 1e-3)
 
-    # work figures and roofline of the dominant kernel (the batched launch)
-    work = {k: 0 for k in ("traversals", "beams", "nonempty", "probes", "paired", "passed")}
-    for t in range(STEPS):
-        w = d.sensor_work(parts_d[t * P:(t + 1) * P], bo_d, D)
-        for k in work:
-            work[k] += w[k]
-    alg_bytes = algorithmic_bytes(work, STEPS * P)
+    work = {}
+    for t in range(S):
+        add_work(work, d.sensor_work(parts_d[t * P:(t + 1) * P], bo_d, D))
+    alg = algorithmic_bytes(work, S * P)
     peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
-    traffic = recorded_traffic("batched_kernel", STEPS * P)
+    achieved = alg / (ms_step * 1e-3) / 1e9
 
     extra = {}
-    # graph replay of the same launch
-    ms_g = timed(lambda: plan.launch_graph(), max(3, args.steps // 2), 2)
+    k2 = max(3, args.steps // 2)
+    ms_g = timed(plan.launch_graph, k2, 2)
     extra["graph_rays_per_s"] = rays_per_step / (statistics.mean(ms_g) * 1e-3)
 
-    # 200 per-filter launches of cddt_sensor_weights (the plain, unbatched path)
     def sequential():
-        for t in range(STEPS):
+        for t in range(S):
             d.sensor_weights(parts_d[t * P:(t + 1) * P], bo_d, obs_d[t], m, D, logw=logw_d[t * P:(t + 1) * P])
-    ms_s = timed(sequential, max(3, args.steps // 2), 2)
+    ms_s = timed(sequential, k2, 2)
     extra["sequential_rays_per_s"] = rays_per_step / (statistics.mean(ms_s) * 1e-3)
-    extra["batched_speedup_vs_sequential"] = statistics.mean(ms_s) / ms_step
+    extra["batched_speedup_vs_sequential"] = statistics.mean(ms_s) / statistics.mean(ms)
 
-    # binary-search layout on the same data
     d.set_search(G.SEARCH_BINARY)
-    ms_b = timed(lambda: plan.run(), max(3, args.steps // 2), 2)
+    ms_b = timed(plan.run, k2, 2)
+    extra["binary_search_launch_groups"] = plan.groups()
     d.set_search(G.SEARCH_TREE)
     extra["binary_search_rays_per_s"] = rays_per_step / (statistics.mean(ms_b) * 1e-3)
 
-    # 10 M-query sweep, uniform over free space
-    sw = torch.from_numpy(wl["sweep"]).to(dev)
-    out = torch.empty(SWEEP, dtype=torch.float32, device=dev)
+    sw = torch.from_numpy(w["sweep"]).to(dev)
+    out = torch.empty(sw.shape[0], dtype=torch.float32, device=dev)
     ms_u = timed(lambda: d.calc_range_many(sw, out=out), 5, 2)
     ms_o = timed(lambda: d.calc_range_many(sw, sort_by_slice=True, out=out), 5, 2)
-    extra["sweep_rays_per_s"] = SWEEP / (statistics.mean(ms_u) * 1e-3)
-    extra["sweep_sorted_rays_per_s"] = SWEEP / (statistics.mean(ms_o) * 1e-3)
+    extra["sweep_rays_per_s"] = sw.shape[0] / (statistics.mean(ms_u) * 1e-3)
+    extra["sweep_sorted_rays_per_s"] = sw.shape[0] / (statistics.mean(ms_o) * 1e-3)
 
-    # pruned CDDT
-    dp = G.CDDT(grid, THETA, MAX_RANGE)
-    try:
-        dp.prune()
-        stp = dp.stats()
-        plan_p = G.Plan(filters_for(dp))
-        plan_p.set_shape(**shape)
-        ms_p = timed(lambda: plan_p.run(), max(3, args.steps // 2), 2)
-        extra["pruned_rays_per_s"] = rays_per_step / (statistics.mean(ms_p) * 1e-3)
-        extra["prune_ms"] = stp["prune_ms"]
-        extra["pruned_zero_points"] = stp["n_zero_points"]
-        ms_pu = timed(lambda: dp.calc_range_many(sw, out=out), 5, 2)
-        extra["pruned_sweep_rays_per_s"] = SWEEP / (statistics.mean(ms_pu) * 1e-3)
-        plan_p.close()
-    except G.CDDTError as e:
-        extra["pruned"] = f"unavailable: {e}"
+    dp = G.CDDT(grid, w["theta_disc"], mr)
+    dp.prune()
+    stp = dp.stats()
+    plan_p = G.Plan(filters_for(dp))
+    plan_p.set_shape(**shape)
+    ms_p = timed(plan_p.run, k2, 2)
+    extra["pruned_rays_per_s"] = rays_per_step / (statistics.mean(ms_p) * 1e-3)
+    extra["prune_ms"] = stp["prune_ms"]
+    extra["pruned_zero_points"] = stp["n_zero_points"]
+    ms_pu = timed(lambda: dp.calc_range_many(sw, out=out), 5, 2)
+    extra["pruned_sweep_rays_per_s"] = sw.shape[0] / (statistics.mean(ms_pu) * 1e-3)
+    plan_p.close()
 
     # end to end through the public API from pinned host buffers
-    parts_h = torch.from_numpy(wl["parts"].reshape(-1, 3)).pin_memory()
+    parts_h = torch.from_numpy(w["parts"].reshape(-1, 3)).pin_memory()
     obs_h = torch.from_numpy(obs).pin_memory()
-    logw_h = torch.empty(STEPS * P, dtype=torch.float32).pin_memory()
+    logw_h = torch.empty(S * P, dtype=torch.float32).pin_memory()
 
     def e2e():
         parts_d.copy_(parts_h, non_blocking=True)
         obs_d.copy_(obs_h, non_blocking=True)
         plan.run()
         logw_h.copy_(logw_d, non_blocking=True)
-    ms_e = timed(e2e, max(3, args.steps // 2), 2)
+    ms_e = timed(e2e, k2, 2)
     e2e_ms = max_over_ranks(world, statistics.mean(ms_e))
 
+    line = base_line(args, world, value, ms_step, "corridor2000",
+                     {"launch": f"persistent batched, autotuned {shape}", "zero_points": st0["n_zero_points"],
+                      "store_bytes": st0["store_bytes"], "occupancy": round(synth.occupancy(w["grid"]), 4)})
+    line.update({
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic("batched_kernel", S * P), "peak_kind": peak_kind,
+                     "kernel": "batched_kernel", "algorithmic_bytes_per_launch": alg, "work": work},
+        "e2e": {"value": world * rays_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(parts_h.numel() * 4 + obs_h.numel() * 4),
+                "d2h_bytes_per_step": int(logw_h.numel() * 4)},
+        "gpu_launches": args.steps, "clocks": clocks,
+        "build_ms": st0["build_ms"], "build_wall_s": build_wall, **extra})
+    if not args.no_cpu and rank == 0:
+        from oracle import oracle as O
+        cores = os.cpu_count() or 1
+        o = O.OracleCDDT(w["grid"], w["theta_disc"], mr)
+        sample = 40
+        dt, n = cpu_oracle_run(o, w["parts"], bo, obs, sample, cores, mr)
+        line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{sample} of {S} filter steps ({n} ray casts), oracle sensor weights, "
+                                          f"OpenMP over particles"}
+    plan.close()
+    return line
+
+
+def bench_rects(args, G, torch, dev, world, rank):
+    w = WL.rects256()
+    bo, D, mr = w["beam_off"], w["D"], w["max_range"]
+    d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], mr)
+    r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], bo)).to(dev)).cpu().numpy()
+    obs = torch.from_numpy(np.clip(r + w["noise"][0], 0, mr).astype(np.float32)).to(dev)
+    parts = torch.from_numpy(w["parts"][0]).to(dev)
+    bo_d = torch.from_numpy(bo).to(dev)
+    logw = torch.empty(parts.shape[0], device=dev)
+    m = G.beam_model(mr)
+    timed = Timer(world, dev)
+    ms = timed(lambda: d.sensor_weights(parts, bo_d, obs, m, D, logw=logw), args.steps, args.warmup)
+    ms_step = max_over_ranks(world, statistics.mean(ms))
+    rays = parts.shape[0] * bo.size
+    plan = G.Plan([dict(map=d, particles=parts, beam_off=bo_d, obs=obs, model=m, logw=logw, pair_offset=D)])
+    plan.autotune()
+    ms_g = timed(plan.launch_graph, args.steps, 2)
+    st = d.stats()
+    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "rects256",
+                     {"launch": "cddt_sensor_weights, one launch per step"})
+    line.update({"gpu_launches": args.steps, "graph_rays_per_s": rays / (statistics.mean(ms_g) * 1e-3),
+                 "build_ms": st["build_ms"], "zero_points": st["n_zero_points"]})
+    plan.close()
+    return line
+
+
+def bench_batched64(args, G, torch, dev, world, rank):
+    w = WL.batched64(seed_offset=rank)
+    bo = torch.from_numpy(w["beam_off"]).to(dev)
+    D = w["D"]
+    filters, build_ms = [], []
+    for mp in w["maps"]:
+        d = G.CDDT(torch.from_numpy(mp["grid"]).to(dev), mp["theta_disc"], mp["max_range"])
+        build_ms.append(d.stats()["build_ms"])
+        r = d.calc_range_many(torch.from_numpy(WL.gt_queries(mp["gt"], w["beam_off"])).to(dev)).cpu().numpy()
+        obs = torch.from_numpy(np.clip(r + mp["noise"][0], 0, mp["max_range"]).astype(np.float32)).to(dev)
+        parts = torch.from_numpy(mp["parts"][0]).to(dev)
+        filters.append(dict(map=d, particles=parts, beam_off=bo, obs=obs, model=G.beam_model(mp["max_range"]),
+                            logw=torch.empty(parts.shape[0], device=dev), pair_offset=D))
+    plan = G.Plan(filters)
+    shape = plan.autotune()
+    timed = Timer(world, dev)
+    rays = sum(f["particles"].shape[0] for f in filters) * bo.numel()
+    with ClockSampler(dev.index) as clk:
+        ms = timed(plan.launch_graph, args.steps, args.warmup)
+    ms_step = max_over_ranks(world, statistics.mean(ms))
+
+    def sequential():
+        for f in filters:
+            f["map"].sensor_weights(f["particles"], bo, f["obs"], f["model"], D, logw=f["logw"])
+    ms_s = timed(sequential, max(3, args.steps // 2), 2)
+    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "batched64",
+                     {"launch": f"persistent batched under a CUDA graph, autotuned {shape}",
+                      "particles": rays // bo.numel()})
+    line.update({"gpu_launches": args.steps, "clocks": clk.summary(),
+                 "sequential_rays_per_s": rays / (statistics.mean(ms_s) * 1e-3),
+                 "batched_speedup_vs_sequential": statistics.mean(ms_s) / statistics.mean(ms),
+                 "build_ms_total": sum(build_ms)})
+    plan.close()
+    return line
+
+
+def bench_diff(args, G, torch, dev, world, rank):
+    w = WL.diff2000(seed_offset=rank)
+    mr = w["max_range"]
+    d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], mr)
+    m = G.beam_model(mr)
+    scans = []
+    for sc in w["scans"]:
+        r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], sc["beam_off"])).to(dev)).cpu().numpy()
+        obs = torch.from_numpy(np.clip(r + sc["noise"], 0, mr).astype(np.float32)).to(dev)
+        scans.append((torch.from_numpy(sc["parts"]).to(dev), torch.from_numpy(sc["beam_off"]).to(dev), obs, sc["D"]))
+    timed = Timer(world, dev)
+
+    def step():  # forward + adjoint, then 10 refinement steps, for both scans
+        for p0, bo, obs, D in scans:
+            x = p0.clone()
+            for _ in range(w["refine_steps"] + 1):
+                lw, g = d.sensor_weights_fwd_bwd(x, bo, obs, m, D)
+                n = torch.linalg.norm(g, dim=1, keepdim=True).clamp_min(1e-12)
+                x[:, :2] += w["eta"] * g / n
+    ms = timed(step, args.steps, args.warmup)
+    ms_step = max_over_ranks(world, statistics.mean(ms))
+    rays = sum(p.shape[0] * bo.numel() for p, bo, _, _ in scans) * (w["refine_steps"] + 1)
+    fwd = timed(lambda: [d.sensor_weights(p, bo, obs, m, D) for p, bo, obs, D in scans], args.steps, 2)
+    rays_fwd = sum(p.shape[0] * bo.numel() for p, bo, _, _ in scans)
+    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "diff2000",
+                     {"launch": "cddt_sensor_weights_fwd_bwd per refinement step (value counts forward+adjoint "
+                                "ray casts)"})
+    line.update({"gpu_launches": args.steps * 2 * (w["refine_steps"] + 1),
+                 "forward_only_rays_per_s": rays_fwd / (statistics.mean(fwd) * 1e-3)})
+    return line
+
+
+def bench_update(args, G, torch, dev, world, rank):
+    w = WL.update4000(steps=args.steps + args.warmup, seed_offset=rank)
+    mr = w["max_range"]
+    grid = torch.from_numpy(w["grid"]).to(dev)
+    d = G.CDDT(grid, w["theta_disc"], mr)
+    st = d.stats()
+    dp = G.CDDT(grid, w["theta_disc"], mr)
+    dp.prune()
+    prune_ms = dp.stats()["prune_ms"]
+    dp.close()
+    bo = torch.from_numpy(w["beam_off"]).to(dev)
+    r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], w["beam_off"])).to(dev)).cpu().numpy()
+    obs = torch.from_numpy(np.clip(r + w["noise"][0], 0, mr).astype(np.float32)).to(dev)
+    parts = torch.from_numpy(w["parts"]).to(dev)
+    m = G.beam_model(mr)
+    logw = torch.empty(parts.shape[0], device=dev)
+    writes = iter([(torch.from_numpy(xy).to(dev), torch.from_numpy(occ).to(dev)) for xy, occ in w["writes"]])
+    upd_ms = []
+
+    def step():
+        xy, occ = next(writes)
+        d.update_cells(xy, occ)
+        upd_ms.append(d.stats()["update_ms"])
+        d.sensor_weights(parts, bo, obs, m, w["D"], logw=logw)
+    timed = Timer(world, dev)
+    ms = timed(step, args.steps, args.warmup)
+    ms_step = max_over_ranks(world, statistics.mean(ms))
+    qms = timed(lambda: d.sensor_weights(parts, bo, obs, m, w["D"], logw=logw), args.steps, 2)
+    rays = parts.shape[0] * bo.numel()
+    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "update4000",
+                     {"writes_per_step": int(w["writes"][0][0].shape[0])})
+    line.update({"update_ms_mean": statistics.mean(upd_ms[args.warmup:] or upd_ms),
+                 "query_only_rays_per_s": rays / (statistics.mean(qms) * 1e-3), "build_ms": st["build_ms"],
+                 "prune_ms": prune_ms, "zero_points": st["n_zero_points"], "store_bytes": st["store_bytes"]})
+    return line
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup()
+    from paper_1705_01167_gb300 import cddt as G
+    G.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fn = {"corridor2000": bench_corridor, "rects256": bench_rects, "batched64": bench_batched64,
+          "diff2000": bench_diff, "update4000": bench_update}[args.workload]
+    line = fn(args, G, torch, dev, world, rank)
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
-                       "inputs": "resident in HBM", "launch": f"persistent batched, autotuned {shape}",
-                       "zero_points": st0["n_zero_points"], "store_bytes": st0["store_bytes"],
-                       "occupancy": round(synth.occupancy(wl["grid"]), 4)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "batched_kernel", "algorithmic_bytes_per_launch": alg_bytes,
-                         "work": work},
-            "e2e": {"value": world * rays_per_step / (e2e_ms * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(parts_h.numel() * 4 + obs_h.numel() * 4),
-                    "d2h_bytes_per_step": int(logw_h.numel() * 4)},
-            "gpu_launches": args.steps,
-            "clocks": clocks,
-            "build_ms": st0["build_ms"], "build_wall_s": build_wall,
-            **extra,
-        }
-        if not args.no_cpu:
-            cores = os.cpu_count() or 1
-            oracle_obs_wl = dict(wl)
-            oracle_obs_wl.pop("_oracle", None)
-            sample = 40
-            dt, rays = cpu_oracle_run(oracle_obs_wl, sample, cores)
-            line["cpu_baseline"] = {"value": rays / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": f"{sample} of {STEPS} filter steps ({rays} ray casts), "
-                                              f"oracle sensor weights, OpenMP over particles"}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -432,25 +556,26 @@ def run_profile(args):
     pass and one sweep launch, a few launches each."""
     import torch
     from paper_1705_01167_gb300 import cddt as G
-    wl = make_workload()
+    w = WL.corridor2000()
     dev = torch.device("cuda", 0)
-    d = G.CDDT(torch.from_numpy(wl["grid"]).to(dev), THETA, MAX_RANGE)
-    bo, D, P = wl["bo"], wl["D"], PARTICLES
-    r = d.calc_range_many(torch.from_numpy(gt_queries(wl["gt"], bo)).to(dev)).cpu().numpy()
-    obs = np.clip(r.reshape(STEPS, BEAMS) + wl["noise"], 0, MAX_RANGE).astype(np.float32)
-    parts_d = torch.from_numpy(wl["parts"].reshape(-1, 3)).to(dev).contiguous()
+    d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], w["max_range"])
+    bo, D = w["beam_off"], w["D"]
+    S, P = w["parts"].shape[:2]
+    r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], bo)).to(dev)).cpu().numpy()
+    obs = np.clip(r.reshape(S, bo.size) + w["noise"], 0, w["max_range"]).astype(np.float32)
+    parts_d = torch.from_numpy(w["parts"].reshape(-1, 3)).to(dev).contiguous()
     bo_d = torch.from_numpy(bo).to(dev)
     obs_d = torch.from_numpy(obs).to(dev).contiguous()
-    logw_d = torch.empty(STEPS * P, dtype=torch.float32, device=dev)
-    m = G.beam_model(MAX_RANGE)
+    logw_d = torch.empty(S * P, dtype=torch.float32, device=dev)
+    m = G.beam_model(w["max_range"])
     plan = G.Plan([dict(map=d, particles=parts_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t], model=m,
-                        logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(STEPS)])
+                        logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(S)])
     plan.set_shape(args.shape_tpp, args.shape_ppi, args.shape_block, args.shape_regcap)
     for _ in range(args.warmup + args.steps):
         plan.run()
-    for t in range(STEPS):
+    for t in range(S):
         d.sensor_weights(parts_d[t * P:(t + 1) * P], bo_d, obs_d[t], m, D, logw=logw_d[t * P:(t + 1) * P])
-    sw = torch.from_numpy(wl["sweep"]).to(dev)
+    sw = torch.from_numpy(w["sweep"]).to(dev)
     d.calc_range_many(sw)
     d.calc_range_many(sw, sort_by_slice=True)
     torch.cuda.synchronize()
@@ -460,19 +585,19 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cddt", choices=["cddt", "reference"])
+    ap.add_argument("--workload", default="corridor2000", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
     ap.add_argument("--shape-tpp", type=int, default=1)
     ap.add_argument("--shape-ppi", type=int, default=512)
     ap.add_argument("--shape-block", type=int, default=512)
     ap.add_argument("--shape-regcap", type=int, default=1)
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="cddt", choices=["cddt", "reference"])
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     if args.profile:
         return run_profile(args)
     if args.impl == "reference":
