@@ -398,6 +398,9 @@ def bench_corridor(args, G, torch, dev, world, rank):
         line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{sample} of {S} filter steps ({n} ray casts), oracle sensor weights, "
                                           f"OpenMP over particles"}
+        dt1, n1 = cpu_oracle_run(o, w["parts"], bo, obs, 4, 1, mr)
+        line["cpu_one_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"4 of {S} filter steps ({n1} ray casts)"}
     plan.close()
     return line
 
