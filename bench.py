@@ -175,32 +175,24 @@ def add_work(acc: dict, w: dict):
 
 # ------------------------------------------------------------------ ranks
 
+from paper_1705_01167_gb300 import ranks as RK  # noqa: E402
+
+
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = RK.env()
     if world > 1:
         import torch
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        RK.init("nccl", world)
     return world, rank, local
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    RK.barrier(world)
 
 
 def max_over_ranks(world, v: float) -> float:
-    if world <= 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return RK.max_over_ranks(world, v, device="cuda")
 
 
 class Timer:
@@ -286,7 +278,7 @@ def run_reference(args):
 # ------------------------------------------------------------------ GPU workloads
 
 def bench_corridor(args, G, torch, dev, world, rank):
-    w = WL.corridor2000(seed_offset=rank)
+    w = WL.corridor2000(seed_offset=RK.seed_offset(rank))
     bo, D, mr = w["beam_off"], w["D"], w["max_range"]
     S, P = w["parts"].shape[:2]
     B = bo.size
@@ -432,7 +424,7 @@ def bench_rects(args, G, torch, dev, world, rank):
 
 
 def bench_batched64(args, G, torch, dev, world, rank):
-    w = WL.batched64(seed_offset=rank)
+    w = WL.batched64(seed_offset=RK.seed_offset(rank))
     bo = torch.from_numpy(w["beam_off"]).to(dev)
     D = w["D"]
     filters, build_ms = [], []
@@ -468,7 +460,7 @@ def bench_batched64(args, G, torch, dev, world, rank):
 
 
 def bench_diff(args, G, torch, dev, world, rank):
-    w = WL.diff2000(seed_offset=rank)
+    w = WL.diff2000(seed_offset=RK.seed_offset(rank))
     mr = w["max_range"]
     d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], mr)
     m = G.beam_model(mr)
@@ -500,7 +492,7 @@ def bench_diff(args, G, torch, dev, world, rank):
 
 
 def bench_update(args, G, torch, dev, world, rank):
-    w = WL.update4000(steps=args.steps + args.warmup, seed_offset=rank)
+    w = WL.update4000(steps=args.steps + args.warmup, seed_offset=RK.seed_offset(rank))
     mr = w["max_range"]
     grid = torch.from_numpy(w["grid"]).to(dev)
     d = G.CDDT(grid, w["theta_disc"], mr)
