@@ -316,7 +316,7 @@ cddt_status cddt_export(cddt_t h, int64_t *slice_base_host, int64_t *bin_start_h
         int64_t o = 0;
         for (int64_t g = 0; g < h->total_bins; ++g) {
             bin_start_host[g] = o;
-            o += hdr[g].n;
+            o += cddt::bin_count(hdr[g].nm);
         }
         bin_start_host[h->total_bins] = o;
     }
@@ -329,7 +329,7 @@ cddt_status cddt_export(cddt_t h, int64_t *slice_base_host, int64_t *bin_start_h
     int s = 0;
     for (int64_t g = 0; g < h->total_bins; ++g) {
         while (s + 1 < h->S && (int64_t)sl[s + 1].sbase <= g) ++s;
-        uint32_t n = hdr[g].n;
+        uint32_t n = cddt::bin_count(hdr[g].nm);
         if (!n) continue;
         size_t leaf = (size_t)(hdr[g].off + cddt::internal_nodes(n, LK, R)) * 32;
         if (h->u16) {

@@ -209,7 +209,7 @@ __global__ void hdr_kernel(const uint32_t *count, const uint32_t *node_off, int6
          g += (int64_t)gridDim.x * blockDim.x) {
         BinHdr b;
         b.off = node_off[g];
-        b.n = count[g];
+        b.nm = count[g];
         for (int q = 0; q < 6; ++q) b.w[q] = 0;
         hdr[g] = b;
         if (count[g]) atomicMax(max_bin, (unsigned long long)count[g]);
@@ -238,7 +238,7 @@ __global__ void scatter_kernel(const uint32_t *cells, int64_t E, int W, const Sl
         for (int b = b0; b <= b1; ++b) {
             uint32_t g = si.sbase + b;
             uint32_t pos = atomicAdd(cursor + g, 1u);
-            KT *run = leaf_run<KT>(store, hdr[g].off, hdr[g].n);
+            KT *run = leaf_run<KT>(store, hdr[g].off, bin_count(hdr[g].nm));
             if (sizeof(KT) == 4)
                 reinterpret_cast<float *>(run)[pos] = xr;
             else
@@ -416,7 +416,7 @@ __global__ void index_kernel(void *store, BinHdr *hdr, int64_t nbins)
     const int lane = threadIdx.x & 31;
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
          g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const uint32_t n = hdr[g].n, off = hdr[g].off;
+        const uint32_t n = bin_count(hdr[g].nm), off = hdr[g].off;
         if (n == 0) continue;
         KT *run = reinterpret_cast<KT *>(store) + ((size_t)off << LK);
         const uint32_t L0 = ((n - 1) >> LK) + 1;
@@ -458,6 +458,8 @@ __global__ void index_kernel(void *store, BinHdr *hdr, int64_t nbins)
             }
             hdr[g].w[lane] = word;
         }
+        __syncwarp();
+        if (lane == 0) hdr[g].nm = n | ((uint32_t)h << 24) | (level_count(L0, LK, h) << 28);
     }
 }
 
@@ -581,6 +583,7 @@ cddt_status layout_bins(cddt_s *h, uint32_t *count_dev, cudaStream_t st, void **
     CDDT_CUDA(cudaStreamSynchronize(st));
     CDDT_CUDA(cudaGetLastError());
     if (host_tot[0] + (uint64_t)extra_nodes > 0xffffffffull) return CDDT_ERR_OOM;
+    if (host_mx > kMaxBinKeys) return CDDT_ERR_ARG;
     int64_t alloc_nodes = (int64_t)host_tot[0] + extra_nodes;
     void *store = nullptr;
     CDDT_CUDA(cudaMalloc(&store, (size_t)std::max<int64_t>(alloc_nodes, 1) * 32));
@@ -619,6 +622,7 @@ static void slice_tables(cddt_s *h, std::vector<SliceInfo> &out)
         si.T = (int32_t)T;
         si.nb = (int32_t)(std::ceil(ymax + T) + 2.0);
         si.sbase = base;
+        si.Tnb = (uint32_t)si.T | ((uint32_t)si.nb << 16);
         si.X = (float)(std::ceil(-xmin) + 1.0);
         base += (uint32_t)si.nb;
         out[s] = si;

@@ -36,22 +36,28 @@ namespace cddt {
 
 constexpr float kInf = __builtin_huge_valf();
 
+// The first 16 bytes hold what a float32 query reads (one 16-byte load).
 struct __align__(16) SliceInfo {
     float c, s;      // cos, sin of theta_s
+    uint32_t sbase;  // first global bin
+    uint32_t Tnb;    // T | nb << 16 (both < 65536)
+    float X;         // 16-bit key offset (integer-valued)
     int32_t T;       // integer bin offset
     int32_t nb;      // bins in the slice
-    uint32_t sbase;  // first global bin
-    float X;         // 16-bit key offset (integer-valued)
-    int32_t pad0, pad1;
+    int32_t pad;
 };
 
 // Everything a query kernel needs to read one CDDT.
 // Per-bin header (see the layout above).
 struct __align__(32) BinHdr {
     uint32_t off;   // first node of the bin's run
-    uint32_t n;     // zero points
+    uint32_t nm;    // zero points n (bits 0-23); once indexed also the stored
+                    // levels h (bits 24-27) and the root's child count (28-31)
     uint32_t w[6];  // root separators, or the keys themselves when n <= R
 };
+
+constexpr uint32_t kMaxBinKeys = (1u << 24) - 1;
+__host__ __device__ __forceinline__ uint32_t bin_count(uint32_t nm) { return nm & 0xffffffu; }
 
 struct MapView {
     const SliceInfo *slices;
@@ -362,7 +368,7 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     r.prev = -kInf;
     uint32_t w[8];
     ld_node(m.hdr + g, pol, w);
-    const uint32_t off = w[0], n = w[1];
+    const uint32_t off = w[0], n = bin_count(w[1]);
     kb = (int)n;
     if (n == 0) return r;
     const Cmp<KT, Upper> cmp(m, x, X);
@@ -377,22 +383,25 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
         return r;
     }
     const uint32_t L0 = ((n - 1) >> LK) + 1;
-    const int h = run_levels(L0, LK, R);
+    const int h = (int)((w[1] >> 24) & 15u);     // stored levels, from the header
+    const int cnt_h = (int)(w[1] >> 28);         // the root's children
     const char *run = reinterpret_cast<const char *>(m.store) + ((size_t)off << 5);
-    if (c >= (int)level_count(L0, LK, h)) {  // every key is below the query
+    if (c >= cnt_h) {  // every key is below the query
         r.idx = (int)n;
         r.prev = load_key<KT>(m, run + ((size_t)internal_nodes(n, LK, R) << 5), (int64_t)n - 1, X);
         return r;
     }
     uint32_t loff = 0, k = (uint32_t)c;
+    uint32_t cnt = (uint32_t)cnt_h;  // nodes at the current level
     for (int l = h; l >= 1; --l) {
         ld_node(run + ((size_t)(loff + k) << 5), pol, w);
         const int cc = count_below<KT, Upper>(w, 0, cmp);
-        loff += level_count(L0, LK, l);
-        // cc < K below the root for any in-map query; the clamp only keeps a
-        // stray comparison inside the level
-        const uint32_t below = level_count(L0, LK, l - 1);
-        k = min(k * K + (uint32_t)cc, below - 1);
+        loff += cnt;
+        cnt = ((L0 - 1) >> (LK * (l - 1))) + 1;  // nodes one level down
+        k = k * K + (uint32_t)cc;
+        // float32 padding never compares below a query; 16-bit padding could
+        // only for a query beyond the map, and the clamp keeps that inside
+        if (sizeof(KT) != 4) k = min(k, cnt - 1);
     }
     // leaf (loff is now the number of internal nodes)
     const char *leaf = run + ((size_t)(loff + k) << 5);
@@ -415,7 +424,7 @@ __device__ __forceinline__ SearchResult binary_search(const MapView &m, uint32_t
     r.prev = -kInf;
     const uint2 on = __ldg(reinterpret_cast<const uint2 *>(m.hdr + g));
     const uint32_t off = on.x;
-    const int n = (int)on.y;
+    const int n = (int)bin_count(on.y);
     kb = n;
     if (n == 0) return r;
     int base = 0, len = n;
@@ -465,7 +474,8 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     k_is_fwd = !bwd;
     const float4 sa = __ldg(reinterpret_cast<const float4 *>(m.slices + s));
     const float c = sa.x, sn = sa.y;
-    const int T = __float_as_int(sa.z), nb = __float_as_int(sa.w);
+    const uint32_t Tnb = __float_as_uint(sa.w);
+    const int T = (int)(Tnb & 0xffffu), nb = (int)(Tnb >> 16);
     float xr, yr;
     project(x, y, c, sn, xr, yr);
     const int b = query_bin(yr, T);
@@ -474,9 +484,8 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     f.dzx = f.dzy = r.dzx = r.dzy = 0.0f;
     f.kb = r.kb = -1;
     if (b >= 0 && b < nb) {
-        const float2 sb = __ldg(reinterpret_cast<const float2 *>(m.slices + s) + 2);
-        const uint32_t g = __float_as_uint(sb.x) + (uint32_t)b;
-        const float X = sb.y;
+        const uint32_t g = __float_as_uint(sa.z) + (uint32_t)b;
+        const float X = sizeof(KT) == 4 ? 0.0f : __ldg(&m.slices[s].X);
         int kb;
         if (!bwd || pair) {
             // forward: first key > x' (upper bound)
@@ -493,7 +502,7 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
                     const uint2 on = __ldg(reinterpret_cast<const uint2 *>(m.hdr + g));
                     while (j >= 0 && pv == xr) {
                         --j;
-                        if (j >= 0) pv = bin_key<KT>(m, on.x, on.y, j, X);
+                        if (j >= 0) pv = bin_key<KT>(m, on.x, bin_count(on.y), j, X);
                     }
                 }
                 if (j >= 0) {

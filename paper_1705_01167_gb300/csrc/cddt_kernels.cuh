@@ -74,7 +74,7 @@ struct Segs {
     __device__ __forceinline__ void get(uint32_t id, KT *&p, uint32_t &n) const
     {
         if (hdr) {
-            n = hdr[id].n;
+            n = bin_count(hdr[id].nm);
             p = leaf_run<KT>(store, hdr[id].off, n);
         } else {
             n = len[id];

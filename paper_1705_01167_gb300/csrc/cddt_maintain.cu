@@ -65,12 +65,13 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep)
         for (int b = b0; b <= b1; ++b) {
             const uint32_t g = si.sbase + (uint32_t)b;
             const BinHdr bh = m.hdr[g];
-            if (bh.n == 0) continue;
+            const uint32_t bn = bin_count(bh.nm);
+            if (bn == 0) continue;
             int kb;
             const int l = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, si.X, pol, kb).idx;  // first key >= xlo
             const int u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, si.X, pol, kb).idx;   // first key > xhi
-            const int m0 = max(l - 1, 0), m1 = min(u, (int)bh.n - 1);
-            uint8_t *kp = keep + (((size_t)bh.off + internal_nodes(bh.n, LK, KeyT<KT>::R)) << LK);
+            const int m0 = max(l - 1, 0), m1 = min(u, (int)bn - 1);
+            uint8_t *kp = keep + (((size_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK);
             for (int mm = m0; mm <= m1; ++mm) kp[mm] = 1;
         }
     }
@@ -84,9 +85,10 @@ __global__ void count_kept_kernel(const BinHdr *hdr, int64_t nbins, const uint8_
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
          g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const BinHdr bh = hdr[g];
-        const uint8_t *kp = keep + (((size_t)bh.off + internal_nodes(bh.n, LK, KeyT<KT>::R)) << LK);
+        const uint32_t bn = bin_count(bh.nm);
+        const uint8_t *kp = keep + (((size_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK);
         uint32_t c = 0;
-        for (uint32_t i = lane; i < bh.n; i += 32) c += kp[i];
+        for (uint32_t i = lane; i < bn; i += 32) c += kp[i];
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0) cnt[g] = c;
     }
@@ -102,17 +104,18 @@ __global__ void compact_kernel(void *old_store, const BinHdr *old_hdr, const uin
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
          g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const BinHdr ob = old_hdr[g], nb = new_hdr[g];
-        const KT *src = leaf_run<KT>(old_store, ob.off, ob.n);
-        const uint8_t *kp = keep + (((size_t)ob.off + internal_nodes(ob.n, LK, KeyT<KT>::R)) << LK);
-        KT *dst = leaf_run<KT>(new_store, nb.off, nb.n);
+        const uint32_t on = bin_count(ob.nm), nn = bin_count(nb.nm);
+        const KT *src = leaf_run<KT>(old_store, ob.off, on);
+        const uint8_t *kp = keep + (((size_t)ob.off + internal_nodes(on, LK, KeyT<KT>::R)) << LK);
+        KT *dst = leaf_run<KT>(new_store, nb.off, nn);
         uint32_t o = 0;
-        for (uint32_t i0 = 0; i0 < ob.n; i0 += 32) {
+        for (uint32_t i0 = 0; i0 < on; i0 += 32) {
             const uint32_t i = i0 + lane;
-            const bool k = i < ob.n && kp[i];
+            const bool k = i < on && kp[i];
             const unsigned msk = __ballot_sync(0xffffffffu, k);
             if (k) {
                 const uint32_t pos = o + __popc(msk & ((1u << lane) - 1));
-                if (pos < nb.n) dst[pos] = src[i];
+                if (pos < nn) dst[pos] = src[i];
             }
             o += __popc(msk);
         }
@@ -276,7 +279,7 @@ __global__ void upd_newcount_kernel(const BinHdr *hdr, const uint32_t *ins_n, co
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
          g += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t n = hdr[g].n, d = del_n[g];
+        const uint32_t n = bin_count(hdr[g].nm), d = del_n[g];
         if (d > n) flag_error(status);
         new_n[g] = n + ins_n[g] - min(d, n);
     }
@@ -319,9 +322,10 @@ __global__ void upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, v
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
          g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const BinHdr ob = old_hdr[g], nb = new_hdr[g];
-        const KT *old = leaf_run<KT>(const_cast<void *>(old_store), ob.off, ob.n);
-        KT *dst = leaf_run<KT>(new_store, nb.off, nb.n);
-        const int n = (int)ob.n, ni = (int)ins_n[g], nd = (int)min(del_n[g], ob.n), nn = (int)nb.n;
+        const uint32_t obn = bin_count(ob.nm), nbn = bin_count(nb.nm);
+        const KT *old = leaf_run<KT>(const_cast<void *>(old_store), ob.off, obn);
+        KT *dst = leaf_run<KT>(new_store, nb.off, nbn);
+        const int n = (int)obn, ni = (int)ins_n[g], nd = (int)min(del_n[g], obn), nn = (int)nbn;
         const KT *I = ins_keys + ins_off[g];
         const KT *Dl = del_keys + del_off[g];
         if (ni == 0 && nd == 0) {
