@@ -79,24 +79,27 @@ struct MapView {
 __device__ __forceinline__ bool query_dir(float theta, float inv_step, int N, int &k)
 {
     float t = __fmul_rn(theta, inv_step);
-    float tk = floorf(__fadd_rn(t, 0.5f));
-    // one turn either way is the common case (an in-range heading plus a
-    // beam offset); integers below 2^24 add exactly in float32
-    const float fN = (float)N;
-    if (tk < 0.0f && tk >= -fN) tk = __fadd_rn(tk, fN);
-    else if (tk >= fN && tk < 2.0f * fN) tk = __fsub_rn(tk, fN);
-    if (tk >= 0.0f && tk < fN) {
-        k = (int)tk;
+    const float th = __fadd_rn(t, 0.5f);
+    // floor and convert in one step; within one turn either way of [0, N)
+    // (an in-range heading plus a beam offset) one add or subtract of N wraps
+    // it.  NaN converts to 0, so it is caught first.
+    // Out-of-range values saturate and fall through to the general wrap.
+    int kw = __float2int_rd(th);
+    kw += kw < 0 ? N : 0;
+    kw -= kw >= N ? N : 0;
+    if ((unsigned)kw < (unsigned)N && th == th) {
+        k = kw;
         return true;
     }
+    const float tk = floorf(th);
     if (fabsf(tk) < 16777216.0f) {
-        int ki = (int)tk % N;
+        const int ki = (int)tk % N;
         k = ki < 0 ? ki + N : ki;
         return true;
     }
     if (!isfinite(tk)) return false;
-    int ki = (int)fmodf(tk, (float)N);
-    k = ki < 0 ? ki + N : ki;
+    const int kf = (int)fmodf(tk, (float)N);
+    k = kf < 0 ? kf + N : kf;
     return true;
 }
 
@@ -567,10 +570,15 @@ struct BeamConsts {
     float inv_2s2, norm_hit, inv_s2, inv_sig;
     float lam, max_range, inv_max_range;
     int trunc;
+    float hit_a;   // z_hit / (sigma sqrt(2 pi)): the weighted hit peak
+    float hit_k2;  // log2(e) / (2 sigma^2): hit exponent in base 2
+    float lam_l2;  // lambda log2(e)
+    float pad;
 };
 
 inline BeamConsts make_beam_consts(const cddt_beam_model &m)
 {
+    const double LOG2E = 1.4426950408889634;
     BeamConsts b;
     b.z_hit = m.z_hit;
     b.z_short = m.z_short;
@@ -585,13 +593,18 @@ inline BeamConsts make_beam_consts(const cddt_beam_model &m)
     b.max_range = m.max_range;
     b.inv_max_range = (float)(1.0 / (double)m.max_range);
     b.trunc = m.hit_truncnorm;
+    b.hit_a = (float)((double)m.z_hit / (sig * 2.5066282746310002));
+    b.hit_k2 = (float)(LOG2E / (2.0 * sig * sig));
+    b.lam_l2 = (float)((double)m.lambda_short * LOG2E);
+    b.pad = 0.0f;
     return b;
 }
 
-// Per-beam terms that depend on the measurement only.
+// Per-beam terms that depend on the measurement only; staged in shared
+// memory as one float4 per beam together with the beam's angle offset.
 struct BeamObs {
     float z;      // measured range clamped to [0, max_range]
-    float e_lz;   // lambda e^{-lambda z}
+    float s_lz;   // z_short lambda e^{-lambda z}
     float c_mr;   // z_max [z >= max] + z_rand [z < max] / max_range
 };
 
@@ -600,49 +613,89 @@ __device__ __forceinline__ BeamObs beam_obs(const BeamConsts &m, float obs)
     BeamObs o;
     float z = fminf(fmaxf(obs, 0.0f), m.max_range);
     o.z = z;
-    o.e_lz = m.lam * expf(-m.lam * z);
+    o.s_lz = m.z_short * (m.lam * expf(-m.lam * z));
     o.c_mr = (z >= m.max_range) ? m.z_max : m.z_rand * m.inv_max_range;
     return o;
 }
 
-// log p(z | z*) and, when wanted, d log p / d z*.  The hit exponential and
-// the final logarithm use the hardware approximations (__expf, __logf):
-// their error, a few 1e-7 of log p per beam, is far below the 1e-5 relative
-// parity bar on the particle's sum, and they are a fifth of the fused
-// kernel's instructions in the accurate forms.  The short-reading
-// normaliser 1 - e^{-lambda z*} keeps expm1f, whose argument is often tiny.
+// The hardware base-2 exponential, logarithm and reciprocal (PTX ex2, lg2,
+// rcp .approx): relative errors of a few 2^-23, results below 2^-126 flushed.
+__device__ __forceinline__ float hw_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float hw_log2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float hw_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1 - e^{-u} for u >= 0 given e = e^{-u}.  Below u = 1/2 the difference
+// would cancel, so it is the Maclaurin series u - u^2/2! + u^3/3! - ...
+// through u^9 (truncation below 1.1e-8 relative there); above, 1 - e loses
+// nothing (e <= 0.61).
+__device__ __forceinline__ float one_minus_exp_neg(float u, float e)
+{
+    float t = 2.7557319e-6f;                 //  1/9!
+    t = fmaf(t, -u, 2.4801587e-5f);          //  1/8!
+    t = fmaf(t, -u, 1.9841270e-4f);          //  1/7!
+    t = fmaf(t, -u, 1.3888889e-3f);          //  1/6!
+    t = fmaf(t, -u, 8.3333333e-3f);          //  1/5!
+    t = fmaf(t, -u, 4.1666667e-2f);          //  1/4!
+    t = fmaf(t, -u, 1.6666667e-1f);          //  1/3!
+    t = fmaf(t, -u, 0.5f);                   //  1/2!
+    t = fmaf(t, -u, 1.0f);
+    return u < 0.5f ? u * t : 1.0f - e;
+}
+
+constexpr float kLn2 = 0.69314718055994531f;
+
+// log2 p(z | z*) and, when wanted, d ln p / d z* (Section VI's beam model:
+// a Gaussian hit, an exponential short reading normalised on [0, z*], a
+// max-range spike and a uniform floor).  Callers multiply the summed log2
+// by ln 2 once per particle.  The exponentials, the reciprocal and the
+// logarithm use the hardware approximations: their error, a few 1e-7 of
+// ln p per beam, is far below the 1e-5 relative parity bar on the
+// particle's sum.  Every term is evaluated and selected, without branches.
 template <bool Grad>
-__device__ __forceinline__ float beam_logp(const BeamConsts &m, const BeamObs &o, float zs, float &dlogp)
+__device__ __forceinline__ float beam_log2p(const BeamConsts &m, const BeamObs &o, float zs, float &dlogp)
 {
     const float d = o.z - zs;
-    float p_hit = m.norm_hit * __expf(-(d * d) * m.inv_2s2);
+    float ph = m.hit_a * hw_exp2(-(d * d) * m.hit_k2);  // z_hit p_hit
     float dhit = 0.0f;
     if (m.trunc) {
         float a = (m.max_range - zs) * m.inv_sig;
         float b = -zs * m.inv_sig;
         float D = normcdff(a) - normcdff(b);
-        p_hit = p_hit / D;
+        ph = ph / D;
         if (Grad) {
             const float r2pi = 0.3989422804014327f;
             float dD = (r2pi * expf(-0.5f * b * b) - r2pi * expf(-0.5f * a * a)) * m.inv_sig;
-            dhit = p_hit * (d * m.inv_s2 - dD / D);
+            dhit = ph * (d * m.inv_s2 - dD / D);
         }
     } else if (Grad) {
-        dhit = p_hit * d * m.inv_s2;
+        dhit = ph * d * m.inv_s2;
     }
-    float p_short = 0.0f, dshort = 0.0f;
-    if (zs > 0.0f && o.z <= zs) {
-        float den = -expm1f(-m.lam * zs);
-        float inv = __fdividef(1.0f, den);
-        p_short = o.e_lz * inv;
-        if (Grad && o.z < zs) {
-            float e = expf(-m.lam * zs);
-            dshort = -m.lam * o.e_lz * e * inv * inv;
-        }
+    // z_short p_short = z_short lambda e^{-lambda z} / (1 - e^{-lambda z*}), 0 < z <= z*
+    const float e = hw_exp2(-zs * m.lam_l2);
+    const float inv = hw_rcp(one_minus_exp_neg(m.lam * zs, e));
+    const bool short_on = zs > 0.0f && o.z <= zs;
+    const float ps = short_on ? o.s_lz * inv : 0.0f;
+    const float p = ph + ps + o.c_mr;
+    if (Grad) {
+        const float dshort = (zs > 0.0f && o.z < zs) ? -m.lam * o.s_lz * e * inv * inv : 0.0f;
+        dlogp = (dhit + dshort) / p;
     }
-    const float p = m.z_hit * p_hit + m.z_short * p_short + o.c_mr;
-    if (Grad) dlogp = (m.z_hit * dhit + m.z_short * dshort) / p;
-    return __logf(p);
+    return hw_log2(p);
 }
 
 }  // namespace cddt

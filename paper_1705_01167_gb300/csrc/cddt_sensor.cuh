@@ -24,7 +24,7 @@ __device__ __forceinline__ int ceil_log2p1(int kb)
 }
 
 // One particle's beams in traversal slots t = lane, lane + TPP, ... ; smem
-// holds phi[B], z[B], e_lz[B], c_mr[B].
+// holds one float4 {phi, z, s_lz, c_mr} per beam.  acc sums log2 p.
 template <typename KT, int MODE, int SEARCH>
 __device__ __forceinline__ void particle_slots(const MapView &m, const SensorArgs &a, const float *sh,
                                                int64_t p, bool valid, int lane, int TPP, uint64_t pol,
@@ -40,7 +40,7 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const SensorArg
     }
     const bool ok = valid && free_cell(m.grid, m.W, m.H, x, y);
     ok_out = ok;
-    const float *phi = sh, *zz = sh + B, *elz = sh + 2 * B, *cmr = sh + 3 * B;
+    const float4 *bt = reinterpret_cast<const float4 *>(sh);
     for (int t = lane; t < T; t += TPP) {
         const int i = t;
         const int j = (D > 0 && t + D < B) ? t + D : -1;
@@ -51,8 +51,8 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const SensorArg
         bool pairdone = false;
         if (ok) {
             int ki = 0, kj = 0;
-            bool vi = query_dir(__fadd_rn(th, phi[i]), m.inv_step, m.N, ki);
-            bool vj = j >= 0 && query_dir(__fadd_rn(th, phi[j]), m.inv_step, m.N, kj);
+            bool vi = query_dir(__fadd_rn(th, sh[4 * i]), m.inv_step, m.N, ki);
+            bool vj = j >= 0 && query_dir(__fadd_rn(th, sh[4 * j]), m.inv_step, m.N, kj);
             int kopp = ki + m.S;
             kopp -= (kopp >= m.N) ? m.N : 0;
             if (vj && vi && kj == kopp) {
@@ -96,23 +96,25 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const SensorArg
             continue;
         }
         {
+            const float4 q = bt[i];
             BeamObs o;
-            o.z = zz[i];
-            o.e_lz = elz[i];
-            o.c_mr = cmr[i];
+            o.z = q.y;
+            o.s_lz = q.z;
+            o.c_mr = q.w;
             float dl = 0.f;
-            float lp = beam_logp<MODE != MODE_FWD>(a.bc, o, ci.r, dl);
+            float lp = beam_log2p<MODE != MODE_FWD>(a.bc, o, ci.r, dl);
             acc += lp;
             if (MODE != MODE_FWD) { gx += dl * ci.dzx; gy += dl * ci.dzy; }
             if (MODE == MODE_FWD && a.ranges && valid) a.ranges[p * B + i] = ci.r;
         }
         if (j >= 0) {
+            const float4 q = bt[j];
             BeamObs o;
-            o.z = zz[j];
-            o.e_lz = elz[j];
-            o.c_mr = cmr[j];
+            o.z = q.y;
+            o.s_lz = q.z;
+            o.c_mr = q.w;
             float dl = 0.f;
-            float lp = beam_logp<MODE != MODE_FWD>(a.bc, o, cj.r, dl);
+            float lp = beam_log2p<MODE != MODE_FWD>(a.bc, o, cj.r, dl);
             acc += lp;
             if (MODE != MODE_FWD) { gx += dl * cj.dzx; gy += dl * cj.dzy; }
             if (MODE == MODE_FWD && a.ranges && valid) a.ranges[p * B + j] = cj.r;
@@ -124,10 +126,7 @@ __device__ __forceinline__ void stage_beams(const SensorArgs &a, float *sh)
 {
     for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
         BeamObs o = beam_obs(a.bc, __ldg(a.obs + i));
-        sh[i] = __ldg(a.beam_off + i);
-        sh[a.B + i] = o.z;
-        sh[2 * a.B + i] = o.e_lz;
-        sh[3 * a.B + i] = o.c_mr;
+        reinterpret_cast<float4 *>(sh)[i] = make_float4(__ldg(a.beam_off + i), o.z, o.s_lz, o.c_mr);
     }
 }
 
@@ -142,7 +141,7 @@ __device__ __forceinline__ float group_sum(float v)
 __device__ __forceinline__ void write_particle(const SensorArgs &a, int MODE, int64_t p, float acc, float gx,
                                                float gy)
 {
-    if (MODE == MODE_FWD || MODE == MODE_FWDBWD) a.logw[p] = acc;
+    if (MODE == MODE_FWD || MODE == MODE_FWDBWD) a.logw[p] = acc * kLn2;
     if (MODE == MODE_BWD) {
         float gl = __ldg(a.grad_logw + p);
         a.grad_xy[2 * p] = gl * gx;
@@ -157,7 +156,7 @@ __device__ __forceinline__ void write_particle(const SensorArgs &a, int MODE, in
 template <typename KT, int MODE, int TPP, int SEARCH>
 __global__ void __launch_bounds__(256, 6) sensor_kernel(MapView m, SensorArgs a)
 {
-    extern __shared__ float sh[];
+    extern __shared__ __align__(16) float sh[];
     stage_beams(a, sh);
     __syncthreads();
     const uint64_t pol = policy_evict_last();
@@ -220,7 +219,7 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
     batched_kernel(const FilterDev *filters, const WorkItem *items, int64_t n_items,
                    unsigned long long *queue, int32_t max_B)
 {
-    extern __shared__ float sh[];
+    extern __shared__ __align__(16) float sh[];
     __shared__ long long cur;
     // the current item's filter descriptor, read by every thread from shared
     // memory (uniform loads) instead of being held in registers
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
             bool ok;
             particle_slots<KT, MODE_FWD, SEARCH>(F.m, F.a, sh, p, valid, lane, TPP, pol, acc, gx, gy, w, ok);
             acc = group_sum<TPP>(acc);
-            if (lane == 0 && valid) F.a.logw[p] = acc;
+            if (lane == 0 && valid) F.a.logw[p] = acc * kLn2;
         }
         __syncthreads();
     }
