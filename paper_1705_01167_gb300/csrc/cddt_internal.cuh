@@ -348,6 +348,29 @@ __device__ __forceinline__ int count_below7(const uint32_t (&w)[8], const Cmp<fl
     return (b2 ? 4 : 0) + (b1 ? 2 : 0) + (b0 ? 1 : 0);
 }
 
+// The same count for a float32 leaf, with the keys either side of the
+// answer taken from the registers: at = key[c] and prev = key[c - 1].  The
+// third comparison looked at key[c] or key[c - 1]; the other one is an odd
+// key chosen by the first two comparisons.  prev_here is false for c = 0
+// (prev then sits at the end of the previous leaf).
+template <bool Upper>
+__device__ __forceinline__ int leaf_count7(const uint32_t (&w)[8], const Cmp<float, Upper> &cmp, uint32_t &at,
+                                           uint32_t &prev, bool &prev_here)
+{
+    const bool b2 = cmp.le(w[3]);
+    const uint32_t m2 = b2 ? w[5] : w[1];           // key[4 b2 + 1]
+    const bool b1 = cmp.le(m2);
+    const uint32_t lo = b1 ? w[2] : w[0], hi = b1 ? w[6] : w[4];
+    const uint32_t m3 = b2 ? hi : lo;                // key[4 b2 + 2 b1]
+    const bool b0 = cmp.le(m3);
+    const uint32_t up = b1 ? (b2 ? w[7] : w[3]) : m2;  // key[4 b2 + 2 b1 + 1]
+    const uint32_t dn = b1 ? m2 : w[3];              // key[4 b2 + 2 b1 - 1] (b2 set when !b1)
+    at = b0 ? up : m3;
+    prev = b0 ? m3 : dn;
+    prev_here = b0 || b1 || b2;
+    return (b2 ? 4 : 0) + (b1 ? 2 : 0) + (b0 ? 1 : 0);
+}
+
 // Number of the six header keys w[2..7] below the query (0..6), the same way:
 // a count of 6 (every key below) needs no third comparison.
 template <bool Upper>
@@ -444,12 +467,21 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     // leaf (loff is now the number of internal nodes)
     const char *leaf = run + ((size_t)(loff + k) << 5);
     ld_node(leaf, w);
-    if constexpr (sizeof(KT) == 4) c = count_below7<Upper>(w, cmp);
-    else c = count_below<KT, Upper>(w, 0, cmp);
-    r.idx = min((int)(k * K) + c, (int)n);
-    const int cl = r.idx - (int)(k * K);  // index inside this leaf (may be -1 .. K)
-    if (r.idx < (int)n) r.at = load_key<KT>(m, leaf, cl, X);
-    if (r.idx > 0) r.prev = load_key<KT>(m, leaf, cl - 1, X);
+    if constexpr (sizeof(KT) == 4) {
+        uint32_t at, prev;
+        bool prev_here;
+        c = leaf_count7<Upper>(w, cmp, at, prev, prev_here);
+        r.idx = (int)(k * K) + c;  // <= n: padding never compares below a query
+        if (r.idx < (int)n) r.at = __uint_as_float(at);
+        if (prev_here) r.prev = __uint_as_float(prev);
+        else if (k > 0) r.prev = load_key<KT>(m, leaf, -1, X);
+    } else {
+        c = count_below<KT, Upper>(w, 0, cmp);
+        r.idx = min((int)(k * K) + c, (int)n);
+        const int cl = r.idx - (int)(k * K);  // index inside this leaf (may be -1 .. K)
+        if (r.idx < (int)n) r.at = load_key<KT>(m, leaf, cl, X);
+        if (r.idx > 0) r.prev = load_key<KT>(m, leaf, cl - 1, X);
+    }
     return r;
 }
 
