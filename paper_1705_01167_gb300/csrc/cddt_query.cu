@@ -264,6 +264,15 @@ struct cddt_plan_s {
     int32_t max_B = 0;
     int32_t tpp = 1, ppi = 512, block = 512, regcap = 0;
     int32_t built_ppi = 0;
+    // one launch per (key type, search) group and batch of at most kHotMax
+    // filters: its item range and the filters' hot table (a kernel parameter)
+    struct Launch {
+        int q;
+        int64_t first, count;
+    };
+    std::vector<Launch> launches;
+    std::vector<cddt::HotTable> tabs;  // one per launch
+    int32_t n_queue = 0;              // queue counters allocated
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -275,38 +284,68 @@ static BatchedFn batched_fn(bool u16, int search, int tpp, int block, int regcap
     return u16 ? batched_fn_u16(search, tpp, block, regcap) : batched_fn_f32(search, tpp, block, regcap);
 }
 
+static int plan_group_of(const cddt_plan_s *p, size_t f)
+{
+    const cddt_s *m = p->filters[f].map;
+    return (m->u16 ? 2 : 0) + (m->search == CDDT_SEARCH_BINARY ? 1 : 0);
+}
+
+// Work items and launches.  Filters are grouped by key type and search
+// layout (one kernel instantiation each) and batched kHotMax at a time;
+// within a launch the largest items go first: long filters start early,
+// short ones fill the tail.  Also rebuilds the hot tables from the handles'
+// current views.
 static cddt_status plan_items(cddt_plan_s *p, cudaStream_t st)
 {
     std::vector<WorkItem> items;
-    for (size_t f = 0; f < p->filters.size(); ++f) {
-        int64_t P = p->filters[f].P;
-        for (int64_t s = 0; s < P; s += p->ppi) {
-            WorkItem w;
-            w.filter = (int32_t)f;
-            w.first = s;
-            w.count = (int32_t)std::min<int64_t>(p->ppi, P - s);
-            items.push_back(w);
+    p->launches.clear();
+    p->tabs.clear();
+    for (int q = 0; q < 5; ++q) p->group_start[q] = 0;
+    for (int q = 0; q < 4; ++q) {
+        std::vector<int32_t> fl;
+        for (size_t f = 0; f < p->filters.size(); ++f)
+            if (p->filters[f].P > 0 && plan_group_of(p, f) == q) fl.push_back((int32_t)f);
+        for (size_t b0 = 0; b0 < fl.size(); b0 += kHotMax) {
+            const size_t nb = std::min<size_t>(kHotMax, fl.size() - b0);
+            HotTable tab;
+            std::memset(&tab, 0, sizeof(tab));
+            const size_t first = items.size();
+            for (size_t i = 0; i < nb; ++i) {
+                const cddt_filter &F = p->filters[fl[b0 + i]];
+                tab.f[i].m = F.map->view();
+                tab.f[i].bc = make_beam_consts(F.model);
+                tab.f[i].B = F.B;
+                tab.f[i].D = F.pair_offset;
+                for (int64_t s0 = 0; s0 < F.P; s0 += p->ppi) {
+                    WorkItem w{};
+                    w.filter = fl[b0 + i];
+                    w.first = s0;
+                    w.count = (int32_t)std::min<int64_t>(p->ppi, F.P - s0);
+                    w.hot = (int32_t)i;
+                    items.push_back(w);
+                }
+            }
+            std::stable_sort(items.begin() + first, items.end(),
+                             [](const WorkItem &a, const WorkItem &b) { return a.count > b.count; });
+            p->launches.push_back({q, (int64_t)first, (int64_t)(items.size() - first)});
+            p->tabs.push_back(tab);
+            p->group_start[q + 1] += (int64_t)(items.size() - first);
         }
     }
-    // float32 filters' items first, then 16-bit ones (one launch each); within
-    // a key type the largest items first: long filters start early, short
-    // ones fill the tail
-    auto group_of = [&](const WorkItem &w) {
-        const cddt_s *m = p->filters[w.filter].map;
-        return (m->u16 ? 2 : 0) + (m->search == CDDT_SEARCH_BINARY ? 1 : 0);
-    };
-    std::stable_sort(items.begin(), items.end(), [&](const WorkItem &a, const WorkItem &b) {
-        if (group_of(a) != group_of(b)) return group_of(a) < group_of(b);
-        return a.count > b.count;
-    });
-    for (int q = 0; q < 5; ++q) p->group_start[q] = 0;
-    for (const WorkItem &w : items) p->group_start[group_of(w) + 1]++;
     for (int q = 0; q < 4; ++q) p->group_start[q + 1] += p->group_start[q];
     if (p->items_dev) cudaFree(p->items_dev);
     p->items_dev = nullptr;
     p->n_items = (int64_t)items.size();
     CDDT_CUDA(cudaMalloc(&p->items_dev, sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
     CDDT_CUDA(cudaMemcpyAsync(p->items_dev, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st));
+    const int32_t nq = std::max<int32_t>((int32_t)p->launches.size(), 1);
+    if (nq > p->n_queue) {
+        if (p->queue) cudaFree(p->queue);
+        p->queue = nullptr;
+        p->n_queue = 0;
+        CDDT_CUDA(cudaMalloc(&p->queue, sizeof(unsigned long long) * nq));
+        p->n_queue = nq;
+    }
     CDDT_CUDA(cudaStreamSynchronize(st));
     p->built_ppi = p->ppi;
     if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
@@ -361,7 +400,6 @@ cddt_status plan_create(const cddt_filter *filters, int32_t n, cudaStream_t st, 
     for (int32_t f = 0; f < n; ++f) p->max_B = std::max(p->max_B, filters[f].B);
     cddt_status rc = CDDT_OK;
     cudaError_t e = cudaMalloc(&p->filters_dev, sizeof(FilterDev) * std::max(n, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p->queue, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) rc = cuda_status(e);
     if (rc == CDDT_OK) rc = plan_upload(p, st);
     if (rc == CDDT_OK) rc = plan_items(p, st);
@@ -384,14 +422,15 @@ cddt_status plan_run(cddt_plan_s *p, cudaStream_t st)
         cddt_status rc = plan_items(p, st);
         if (rc != CDDT_OK) return rc;
     }
-    CDDT_CUDA(cudaMemsetAsync(p->queue, 0, 4 * sizeof(unsigned long long), st));
+    CDDT_CUDA(cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long) * p->n_queue, st));
     if (p->n_items == 0) return CDDT_OK;
     size_t sm = beam_smem(p->max_B);
     int nsm = 0;
     CDDT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
-    for (int q = 0; q < 4; ++q) {
-        const int64_t first = p->group_start[q];
-        const int64_t count = p->group_start[q + 1] - first;
+    for (size_t li = 0; li < p->launches.size(); ++li) {
+        const int q = p->launches[li].q;
+        const int64_t first = p->launches[li].first;
+        const int64_t count = p->launches[li].count;
         if (count == 0) continue;
         const bool u16 = q >= 2;
         const int search = (q & 1) ? CDDT_SEARCH_BINARY : CDDT_SEARCH_TREE;
@@ -402,7 +441,8 @@ cddt_status plan_run(cddt_plan_s *p, cudaStream_t st)
         CDDT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, p->block, sm));
         int64_t blocks = (int64_t)std::max(blocks_per_sm, 1) * nsm;
         if (blocks > count) blocks = count;
-        fn<<<(unsigned)blocks, p->block, sm, st>>>(p->filters_dev, p->items_dev + first, count, p->queue + q, p->max_B);
+        fn<<<(unsigned)blocks, p->block, sm, st>>>(p->tabs[li], p->filters_dev, p->items_dev + first, count,
+                                                   p->queue + li, p->max_B);
     }
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;

@@ -25,18 +25,21 @@ __device__ __forceinline__ int ceil_log2p1(int kb)
 
 // One particle's beams in traversal slots t = lane, lane + TPP, ... ; smem
 // holds one float4 {phi, z, s_lz, c_mr} per beam.  acc sums log2 p.
+// m and bc are read where they lie (kernel parameters or shared memory); the
+// particle poses come from `part`, ranges (forward mode, optional) go to
+// `ranges`.
 template <typename KT, int MODE, int SEARCH>
-__device__ __forceinline__ void particle_slots(const MapView &m, const SensorArgs &a, const float *sh,
-                                               int64_t p, bool valid, int lane, int TPP, uint64_t pol,
-                                               float &acc, float &gx, float &gy, WorkAcc &w, bool &ok_out)
+__device__ __forceinline__ void particle_slots(const MapView &m, const BeamConsts &bc, int B, int D,
+                                               const float *part, float *ranges, const float *sh, int64_t p,
+                                               bool valid, int lane, int TPP, uint64_t pol, float &acc, float &gx,
+                                               float &gy, WorkAcc &w, bool &ok_out)
 {
-    const int B = a.B, D = a.D;
     const int T = D > 0 ? D : B;
     float x = 0.f, y = 0.f, th = 0.f;
     if (valid) {
-        x = __ldg(a.part + 3 * p);
-        y = __ldg(a.part + 3 * p + 1);
-        th = __ldg(a.part + 3 * p + 2);
+        x = __ldg(part + 3 * p);
+        y = __ldg(part + 3 * p + 1);
+        th = __ldg(part + 3 * p + 2);
     }
     const bool ok = valid && free_cell(m.grid, m.W, m.H, x, y);
     ok_out = ok;
@@ -102,10 +105,10 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const SensorArg
             o.s_lz = q.z;
             o.c_mr = q.w;
             float dl = 0.f;
-            float lp = beam_log2p<MODE != MODE_FWD>(a.bc, o, ci.r, dl);
+            float lp = beam_log2p<MODE != MODE_FWD>(bc, o, ci.r, dl);
             acc += lp;
             if (MODE != MODE_FWD) { gx += dl * ci.dzx; gy += dl * ci.dzy; }
-            if (MODE == MODE_FWD && a.ranges && valid) a.ranges[p * B + i] = ci.r;
+            if (MODE == MODE_FWD && ranges && valid) ranges[p * B + i] = ci.r;
         }
         if (j >= 0) {
             const float4 q = bt[j];
@@ -114,19 +117,20 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const SensorArg
             o.s_lz = q.z;
             o.c_mr = q.w;
             float dl = 0.f;
-            float lp = beam_log2p<MODE != MODE_FWD>(a.bc, o, cj.r, dl);
+            float lp = beam_log2p<MODE != MODE_FWD>(bc, o, cj.r, dl);
             acc += lp;
             if (MODE != MODE_FWD) { gx += dl * cj.dzx; gy += dl * cj.dzy; }
-            if (MODE == MODE_FWD && a.ranges && valid) a.ranges[p * B + j] = cj.r;
+            if (MODE == MODE_FWD && ranges && valid) ranges[p * B + j] = cj.r;
         }
     }
 }
 
-__device__ __forceinline__ void stage_beams(const SensorArgs &a, float *sh)
+__device__ __forceinline__ void stage_beams(const BeamConsts &bc, int B, const float *obs, const float *beam_off,
+                                            float *sh)
 {
-    for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
-        BeamObs o = beam_obs(a.bc, __ldg(a.obs + i));
-        reinterpret_cast<float4 *>(sh)[i] = make_float4(__ldg(a.beam_off + i), o.z, o.s_lz, o.c_mr);
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        BeamObs o = beam_obs(bc, __ldg(obs + i));
+        reinterpret_cast<float4 *>(sh)[i] = make_float4(__ldg(beam_off + i), o.z, o.s_lz, o.c_mr);
     }
 }
 
@@ -157,7 +161,7 @@ template <typename KT, int MODE, int TPP, int SEARCH>
 __global__ void __launch_bounds__(256, 6) sensor_kernel(MapView m, SensorArgs a)
 {
     extern __shared__ __align__(16) float sh[];
-    stage_beams(a, sh);
+    stage_beams(a.bc, a.B, a.obs, a.beam_off, sh);
     __syncthreads();
     const uint64_t pol = policy_evict_last();
     const int lane = threadIdx.x % TPP;
@@ -170,7 +174,8 @@ __global__ void __launch_bounds__(256, 6) sensor_kernel(MapView m, SensorArgs a)
         const bool valid = p < a.P;
         float acc = 0.f, gx = 0.f, gy = 0.f;
         bool ok;
-        particle_slots<KT, MODE, SEARCH>(m, a, sh, p, valid, lane, TPP, pol, acc, gx, gy, w, ok);
+        particle_slots<KT, MODE, SEARCH>(m, a.bc, a.B, a.D, a.part, a.ranges, sh, p, valid, lane, TPP, pol, acc,
+                                         gx, gy, w, ok);
         if (MODE == MODE_WORK) {
             passed += (ok && lane == 0);
             continue;
@@ -202,10 +207,26 @@ struct __align__(16) FilterDev {
     int32_t pad[3];
 };
 
+// What the traversal loop reads of a filter, passed to the batched kernel as
+// a __grid_constant__ parameter: reads go through the constant cache (LDC)
+// rather than the L1 data path, which the tree searches keep busy.
+struct HotFilter {
+    MapView m;
+    BeamConsts bc;
+    int32_t B, D;
+};
+constexpr int kHotMax = 220;  // filters per batched launch
+struct HotTable {
+    HotFilter f[kHotMax];
+};
+static_assert(sizeof(HotTable) + 512 <= 32764, "kernel parameters are limited to 32764 bytes");
+
 struct WorkItem {
-    int32_t filter;
+    int32_t filter;  // index into the plan's filters
     int32_t count;
     int64_t first;
+    int32_t hot;     // index into the launch's HotTable
+    int32_t pad;
 };
 
 // Persistent batched sensor model: blocks take (filter, particle range)
@@ -216,8 +237,8 @@ struct WorkItem {
 // item range).
 template <typename KT, int SEARCH, int TPP, int BLOCK, int WARPS>
 __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
-    batched_kernel(const FilterDev *filters, const WorkItem *items, int64_t n_items,
-                   unsigned long long *queue, int32_t max_B)
+    batched_kernel(const __grid_constant__ HotTable tab, const FilterDev *filters, const WorkItem *items,
+                   int64_t n_items, unsigned long long *queue, int32_t max_B)
 {
     extern __shared__ __align__(16) float sh[];
     __shared__ long long cur;
@@ -239,7 +260,8 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
         for (int q = threadIdx.x; q < kWords; q += blockDim.x)
             reinterpret_cast<int4 *>(&F)[q] = reinterpret_cast<const int4 *>(filters + wi.filter)[q];
         __syncthreads();
-        stage_beams(F.a, sh);
+        const HotFilter &H = tab.f[wi.hot];
+        stage_beams(H.bc, H.B, F.a.obs, F.a.beam_off, sh);
         __syncthreads();
         WorkAcc w;
         for (int64_t pb = wi.first; pb < wi.first + wi.count; pb += ppb) {
@@ -247,7 +269,8 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
             const bool valid = p < wi.first + wi.count;
             float acc = 0.f, gx = 0.f, gy = 0.f;
             bool ok;
-            particle_slots<KT, MODE_FWD, SEARCH>(F.m, F.a, sh, p, valid, lane, TPP, pol, acc, gx, gy, w, ok);
+            particle_slots<KT, MODE_FWD, SEARCH>(H.m, H.bc, H.B, H.D, F.a.part, nullptr, sh, p, valid, lane, TPP,
+                                                 pol, acc, gx, gy, w, ok);
             acc = group_sum<TPP>(acc);
             if (lane == 0 && valid) F.a.logw[p] = acc * kLn2;
         }
@@ -258,7 +281,8 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
 
 inline size_t beam_smem(int B) { return sizeof(float) * 4 * (size_t)B; }
 
-typedef void (*BatchedFn)(const FilterDev *, const WorkItem *, int64_t, unsigned long long *, int32_t);
+typedef void (*BatchedFn)(const HotTable, const FilterDev *, const WorkItem *, int64_t, unsigned long long *,
+                          int32_t);
 
 // Kernel pointer of the batched kernel for a key type and launch shape
 // (cddt_batched_f32.cu, cddt_batched_u16.cu); nullptr for an unknown shape.
