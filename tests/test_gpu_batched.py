@@ -130,3 +130,35 @@ def test_plan_argument_errors(G, batch):
     with pytest.raises(G.CDDTError):
         plan.set_shape(1, 64, 300)
     plan.close()
+
+
+def test_plan_more_filters_than_one_launch(G, oracle):
+    """More filters than one launch's parameter table holds: the plan splits
+    them over several launches, each with its own table and queue."""
+    g = synth.rect_map(96, 80, seed=950)
+    mr = 120.0
+    d = G.CDDT(dev(g), 36, mr)
+    o = oracle.OracleCDDT(g, 36, mr)
+    n = 2 * 220 + 17
+    filters, refs = [], []
+    for fi in range(n):
+        B = 5 + fi % 7
+        P = 1 + (7 * fi) % 23
+        bo = synth.beam_offsets(B)
+        D = synth.pair_offset(B)
+        gt = synth.uniform_particles(g, 1, seed=5000 + fi)[0]
+        obs = gc.observations(o, gt, bo, mr, seed=6000 + fi)
+        parts = synth.tracking_particles(gt.astype(np.float64), P, seed=7000 + fi)
+        filters.append(dict(map=d, particles=dev(parts).reshape(-1, 3), beam_off=dev(bo), obs=dev(obs),
+                            model=G.beam_model(mr), logw=torch.full((P,), float("nan"), device="cuda"),
+                            pair_offset=D))
+        refs.append(o.sensor_weights(parts, bo, obs, oracle.beam_model(mr), nthreads=1))
+    plan = G.Plan(filters)
+    assert plan.groups()[0] == n  # one item per filter at the default shape
+    plan.run()
+    _check(filters, refs)
+    for f in filters:
+        f["logw"].fill_(float("nan"))
+    plan.launch_graph()
+    _check(filters, refs)
+    plan.close()
