@@ -40,6 +40,9 @@ void free_handle(cddt_s *h)
     cudaFree(h->last_writer);
     cudaFree(h->stamp);
     cudaFree(h->qscratch);
+    cudaFree(h->spare);
+    cudaFree(h->ws);
+    cudaFree(h->ws_keys);
     delete h;
 }
 

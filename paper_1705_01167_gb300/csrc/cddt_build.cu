@@ -205,14 +205,23 @@ __global__ void nodes_kernel(const uint32_t *count, int64_t nbins, uint32_t *nod
 __global__ void hdr_kernel(const uint32_t *count, const uint32_t *node_off, int64_t nbins, BinHdr *hdr,
                            unsigned long long *max_bin)
 {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbins;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        BinHdr b;
-        b.off = node_off[g];
-        b.nm = count[g];
-        for (int q = 0; q < 6; ++q) b.w[q] = 0;
-        hdr[g] = b;
-        if (count[g]) atomicMax(max_bin, (unsigned long long)count[g]);
+    // whole warps step together (blockDim is a multiple of 32), so the
+    // warp's largest count takes one atomic
+    const int lane = threadIdx.x & 31;
+    for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); g0 < nbins;
+         g0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = g0 + lane;
+        unsigned m = 0;
+        if (g < nbins) {
+            BinHdr b;
+            b.off = node_off[g];
+            b.nm = count[g];
+            for (int q = 0; q < 6; ++q) b.w[q] = 0;
+            hdr[g] = b;
+            m = b.nm;
+        }
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && m) atomicMax(max_bin, (unsigned long long)m);
     }
 }
 
@@ -267,19 +276,34 @@ constexpr uint32_t kBigSortMax = 16384;
 template <typename KT>
 __global__ void classify_kernel(Segs<KT> sg, int64_t nseg, uint32_t *lists, uint32_t *list_n, int64_t cap)
 {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nseg;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        KT *p;
-        uint32_t n;
-        sg.get((uint32_t)g, p, n);
-        int cls;
-        if (n <= 1) continue;
-        if (n <= kWarpSortMax) cls = 0;
-        else if (n <= kBlockSortMax) cls = 1;
-        else if (n <= kBigSortMax) cls = 2;
-        else cls = 3;
-        uint32_t pos = atomicAdd(list_n + cls, 1u);
-        lists[cls * cap + pos] = (uint32_t)g;
+    // whole warps step together (blockDim is a multiple of 32): one atomic
+    // per warp and size class
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); g0 < nseg;
+         g0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = g0 + lane;
+        int cls = -1;  // segments of 0 or 1 keys are sorted already
+        if (g < nseg) {
+            KT *p;
+            uint32_t n;
+            sg.get((uint32_t)g, p, n);
+            const bool skip = sg.skip_upto && n <= sg.skip_upto &&
+                              (!sg.also_len || sg.also_len[g] <= sg.skip_upto);
+            if (n <= 1 || skip) cls = -1;
+            else if (n <= kWarpSortMax) cls = 0;
+            else if (n <= kBlockSortMax) cls = 1;
+            else if (n <= kBigSortMax) cls = 2;
+            else cls = 3;
+        }
+        for (int c = 0; c < 4; ++c) {
+            const unsigned mine = __ballot_sync(0xffffffffu, cls == c);
+            if (!mine) continue;
+            uint32_t base = 0;
+            if (lane == __ffs(mine) - 1) base = atomicAdd(list_n + c, (unsigned)__popc(mine));
+            base = __shfl_sync(0xffffffffu, base, __ffs(mine) - 1);
+            if (cls == c) lists[c * cap + base + __popc(mine & lt)] = (uint32_t)g;
+        }
     }
 }
 
@@ -402,83 +426,35 @@ __global__ void copy_back_kernel(const KT *src, uint32_t n, KT *dst)
 // the root's separators over the top stored level, or the keys themselves
 // when the bin has at most R keys.
 template <typename KT>
-__device__ __forceinline__ uint32_t key_bits(KT v)
-{
-    if (sizeof(KT) == 4) return __float_as_uint(*reinterpret_cast<const float *>(&v));
-    return (uint32_t)(*reinterpret_cast<const uint16_t *>(&v));
-}
-
-template <typename KT>
 __global__ void index_kernel(void *store, BinHdr *hdr, int64_t nbins)
 {
-    constexpr int LK = KeyT<KT>::LK;
-    constexpr int R = KeyT<KT>::R;
     const int lane = threadIdx.x & 31;
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
-         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const uint32_t n = bin_count(hdr[g].nm), off = hdr[g].off;
-        if (n == 0) continue;
-        KT *run = reinterpret_cast<KT *>(store) + ((size_t)off << LK);
-        const uint32_t L0 = ((n - 1) >> LK) + 1;
-        const int h = run_levels(L0, LK, R);
-        const uint32_t internal = internal_nodes(n, LK, R);
-        KT *leaves = run + ((size_t)internal << LK);
-        for (uint32_t i = n + lane; i < (L0 << LK); i += 32) leaves[i] = pad_key<KT>();
-        uint32_t loff = 0;
-        for (int l = h; l >= 1; --l) {
-            const uint32_t cnt = level_count(L0, LK, l);
-            for (uint32_t slot = lane; slot < (cnt << LK); slot += 32) {
-                const uint64_t first = (uint64_t)slot << (LK * l);
-                KT v = pad_key<KT>();
-                if (first < n) {
-                    uint64_t last = ((uint64_t)slot + 1) << (LK * l);
-                    if (last > n) last = n;
-                    v = leaves[last - 1];
-                }
-                run[((size_t)loff << LK) + slot] = v;
-            }
-            loff += cnt;
-        }
-        // header separators: R keys packed into 6 words
-        if (lane < 6) {
-            uint32_t word = 0;
-            const uint32_t cnt_h = level_count(L0, LK, h);
-            const int per = 4 / (int)sizeof(KT);  // keys per word
-            for (int e = 0; e < per; ++e) {
-                const uint32_t q = (uint32_t)(lane * per + e);
-                KT v = pad_key<KT>();
-                if (n <= (uint32_t)R) {
-                    if (q < n) v = leaves[q];
-                } else if (q < cnt_h) {
-                    uint64_t last = ((uint64_t)q + 1) << (LK * (h + 1));
-                    if (last > n) last = n;
-                    v = leaves[last - 1];
-                }
-                word |= key_bits<KT>(v) << (16 * e);
-            }
-            hdr[g].w[lane] = word;
-        }
-        __syncwarp();
-        if (lane == 0) hdr[g].nm = n | ((uint32_t)h << 24) | (level_count(L0, LK, h) << 28);
-    }
+         g += ((int64_t)gridDim.x * blockDim.x) >> 5)
+        index_bin<KT>(store, hdr, g, lane);
 }
 
 // ------------------------------------------------------------ host
 
 // Sort every segment ascending, by size class.  Synchronises `st`.
 template <typename KT>
-cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st)
+cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st, Arena *ws)
 {
     if (nseg == 0) return CDDT_OK;
-    Buf lists, list_n;
-    CDDT_CUDA(lists.alloc(sizeof(uint32_t) * 4 * (size_t)nseg));
-    CDDT_CUDA(list_n.alloc(sizeof(uint32_t) * 4));
-    CDDT_CUDA(cudaMemsetAsync(list_n.p, 0, sizeof(uint32_t) * 4, st));
-    classify_kernel<KT><<<grid_for(nseg, 256), 256, 0, st>>>(sg, nseg, lists.as<uint32_t>(), list_n.as<uint32_t>(), nseg);
+    Buf lists_b, list_n_b;
+    uint32_t *L = ws ? ws->take<uint32_t>(4 * (size_t)nseg) : nullptr;
+    uint32_t *LN = ws ? ws->take<uint32_t>(4) : nullptr;
+    if (!L || !LN) {
+        CDDT_CUDA(lists_b.alloc(sizeof(uint32_t) * 4 * (size_t)nseg));
+        CDDT_CUDA(list_n_b.alloc(sizeof(uint32_t) * 4));
+        L = lists_b.as<uint32_t>();
+        LN = list_n_b.as<uint32_t>();
+    }
+    CDDT_CUDA(cudaMemsetAsync(LN, 0, sizeof(uint32_t) * 4, st));
+    classify_kernel<KT><<<grid_for(nseg, 256), 256, 0, st>>>(sg, nseg, L, LN, nseg);
     uint32_t cnt[4];
-    CDDT_CUDA(cudaMemcpyAsync(cnt, list_n.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    CDDT_CUDA(cudaMemcpyAsync(cnt, LN, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CDDT_CUDA(cudaStreamSynchronize(st));
-    uint32_t *L = lists.as<uint32_t>();
     if (cnt[0]) warp_sort_kernel<KT><<<grid_for((int64_t)cnt[0] * 32, 256), 256, 0, st>>>(sg, L, cnt[0]);
     if (cnt[1]) {
         size_t sm = sizeof(KT) * kBlockSortMax;
@@ -519,8 +495,8 @@ cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st)
     return CDDT_OK;
 }
 
-template cddt_status sort_segments<float>(const Segs<float> &, int64_t, cudaStream_t);
-template cddt_status sort_segments<uint16_t>(const Segs<uint16_t> &, int64_t, cudaStream_t);
+template cddt_status sort_segments<float>(const Segs<float> &, int64_t, cudaStream_t, Arena *);
+template cddt_status sort_segments<uint16_t>(const Segs<uint16_t> &, int64_t, cudaStream_t, Arena *);
 
 cddt_status index_store(cddt_s *h, cudaStream_t st)
 {
@@ -549,48 +525,69 @@ cddt_status sort_and_index_any(cddt_s *h, cudaStream_t st)
 // Lay out bins from per-bin counts: node offsets, bins[], store allocation.
 // count_dev is consumed (overwritten).  Synchronises `st`.
 cddt_status layout_bins(cddt_s *h, uint32_t *count_dev, cudaStream_t st, void **store_out,
-                        int64_t *nodes_out, int64_t extra_nodes)
+                        int64_t *nodes_out, int64_t extra_nodes, Arena *ws, void **spare, int64_t *spare_nodes)
 {
     int64_t nb = h->total_bins;
     const int LK = h->u16 ? 4 : 3;
-    Buf nodes, scratch, tot, mx;
-    CDDT_CUDA(nodes.alloc(sizeof(uint32_t) * (size_t)nb));
-    CDDT_CUDA(scratch.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nb)));
-    CDDT_CUDA(tot.alloc(sizeof(uint64_t) * 2));
-    CDDT_CUDA(mx.alloc(sizeof(unsigned long long)));
-    CDDT_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), st));
-    if (LK == 3) nodes_kernel<3, KeyT<float>::R><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
-    else nodes_kernel<4, KeyT<uint16_t>::R><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes.as<uint32_t>());
-    exclusive_scan_u32(nodes.as<uint32_t>(), nodes.as<uint32_t>(), nb, scratch.as<uint64_t>(), tot.as<uint64_t>(), st);
-    // total zero points: scan the counts too (into scratch space of `tot`)
-    Buf zscratch;
-    CDDT_CUDA(zscratch.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nb)));
+    Buf nodes_b, scratch_b, zscratch_b, tot_b;
+    uint32_t *nodes = nullptr;
+    uint64_t *scratch = nullptr, *zscratch = nullptr, *tot = nullptr;
+    if (ws) {
+        nodes = ws->take<uint32_t>((size_t)nb);
+        scratch = ws->take<uint64_t>((size_t)scan_scratch_elems(nb));
+        zscratch = ws->take<uint64_t>((size_t)scan_scratch_elems(nb));
+        tot = ws->take<uint64_t>(3);
+    }
+    if (!nodes || !scratch || !zscratch || !tot) {
+        CDDT_CUDA(nodes_b.alloc(sizeof(uint32_t) * (size_t)nb));
+        CDDT_CUDA(scratch_b.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nb)));
+        CDDT_CUDA(zscratch_b.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nb)));
+        CDDT_CUDA(tot_b.alloc(sizeof(uint64_t) * 3));
+        nodes = nodes_b.as<uint32_t>();
+        scratch = scratch_b.as<uint64_t>();
+        zscratch = zscratch_b.as<uint64_t>();
+        tot = tot_b.as<uint64_t>();
+    }
+    unsigned long long *mx = reinterpret_cast<unsigned long long *>(tot + 2);
+    CDDT_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    if (LK == 3) nodes_kernel<3, KeyT<float>::R><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes);
+    else nodes_kernel<4, KeyT<uint16_t>::R><<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nb, nodes);
+    exclusive_scan_u32(nodes, nodes, nb, scratch, tot, st);
+    // total zero points: reduce the counts too
     {
         int64_t nblk = (nb + kScanTile - 1) / kScanTile;
         if (nblk) {
-            scan_reduce_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(count_dev, nb, zscratch.as<uint64_t>());
-            scan_partials_kernel<<<1, 1024, 0, st>>>(zscratch.as<uint64_t>(), nblk, tot.as<uint64_t>() + 1);
+            scan_reduce_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(count_dev, nb, zscratch);
+            scan_partials_kernel<<<1, 1024, 0, st>>>(zscratch, nblk, tot + 1);
         } else {
-            CDDT_CUDA(cudaMemsetAsync(tot.as<uint64_t>() + 1, 0, sizeof(uint64_t), st));
+            CDDT_CUDA(cudaMemsetAsync(tot + 1, 0, sizeof(uint64_t), st));
         }
     }
-    hdr_kernel<<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nodes.as<uint32_t>(), nb, h->hdr,
-                                                  mx.as<unsigned long long>());
-    uint64_t host_tot[2];
-    unsigned long long host_mx = 0;
-    CDDT_CUDA(cudaMemcpyAsync(host_tot, tot.p, sizeof(host_tot), cudaMemcpyDeviceToHost, st));
-    CDDT_CUDA(cudaMemcpyAsync(&host_mx, mx.p, sizeof(host_mx), cudaMemcpyDeviceToHost, st));
+    hdr_kernel<<<grid_for(nb, 256), 256, 0, st>>>(count_dev, nodes, nb, h->hdr, mx);
+    uint64_t host_tot[3];
+    CDDT_CUDA(cudaMemcpyAsync(host_tot, tot, sizeof(host_tot), cudaMemcpyDeviceToHost, st));
     CDDT_CUDA(cudaStreamSynchronize(st));
     CDDT_CUDA(cudaGetLastError());
     if (host_tot[0] + (uint64_t)extra_nodes > 0xffffffffull) return CDDT_ERR_OOM;
-    if (host_mx > kMaxBinKeys) return CDDT_ERR_ARG;
-    int64_t alloc_nodes = (int64_t)host_tot[0] + extra_nodes;
+    if (host_tot[2] > kMaxBinKeys) return CDDT_ERR_ARG;
+    const int64_t need = std::max<int64_t>((int64_t)host_tot[0], 1);
     void *store = nullptr;
-    CDDT_CUDA(cudaMalloc(&store, (size_t)std::max<int64_t>(alloc_nodes, 1) * 32));
+    if (spare && *spare && *spare_nodes >= need) {
+        store = *spare;
+        *spare = nullptr;
+    } else {
+        if (spare && *spare) {
+            cudaFree(*spare);
+            *spare = nullptr;
+        }
+        const int64_t alloc_nodes = need + extra_nodes;
+        CDDT_CUDA(cudaMalloc(&store, (size_t)alloc_nodes * 32));
+        if (spare_nodes) *spare_nodes = alloc_nodes;
+    }
     *store_out = store;
     *nodes_out = (int64_t)host_tot[0];
     h->n_zp = (int64_t)host_tot[1];
-    h->max_bin = (int64_t)host_mx;
+    h->max_bin = (int64_t)host_tot[2];
     return CDDT_OK;
 }
 

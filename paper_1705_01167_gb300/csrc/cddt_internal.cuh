@@ -765,6 +765,14 @@ struct cddt_s {
     // query sort scratch
     void *qscratch = nullptr;
     int64_t qscratch_bytes = 0;
+    // kept by updates: the previous store (reused as the next update's
+    // target) and grow-only workspaces
+    void *spare = nullptr;
+    int64_t spare_nodes = 0;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *ws_keys = nullptr;
+    size_t ws_keys_bytes = 0;
 
     cddt::MapView view() const
     {
@@ -799,4 +807,10 @@ cddt_status build_index(cddt_s *h, cudaStream_t st);
     do {                                                                      \
         cudaError_t e_ = (call);                                              \
         if (e_ != cudaSuccess) return cddt::cuda_status(e_);                  \
+    } while (0)
+
+#define CDDT_TRY(call)                                                        \
+    do {                                                                      \
+        cddt_status r_ = (call);                                              \
+        if (r_ != CDDT_OK) return r_;                                         \
     } while (0)

@@ -8,11 +8,21 @@
 
 namespace cddt {
 
+struct Arena;
+
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *scratch,
                         uint64_t *total_dev, cudaStream_t st);
 int64_t scan_scratch_elems(int64_t n);
+// Lay out bins of the given key counts: headers (off, count) into h->hdr,
+// and a store of at least that many nodes.  Temporaries come from `ws` when
+// given.  Without `spare` a new store of nodes + extra_nodes is allocated.
+// With `spare`, *spare (a buffer of *spare_nodes nodes, or null) is used
+// when large enough (*spare becomes null), else it is freed and a new
+// store with extra_nodes headroom allocated; *spare_nodes then receives the
+// capacity of the returned store.
 cddt_status layout_bins(cddt_s *h, uint32_t *count_dev, cudaStream_t st, void **store_out,
-                        int64_t *nodes_out, int64_t extra_nodes);
+                        int64_t *nodes_out, int64_t extra_nodes, Arena *ws = nullptr, void **spare = nullptr,
+                        int64_t *spare_nodes = nullptr);
 cddt_status sort_and_index_any(cddt_s *h, cudaStream_t st);
 cddt_status construct(cddt_s *h, cudaStream_t st);
 cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st);
@@ -41,6 +51,22 @@ cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int 
 int64_t sorted_scratch_bytes(const cddt_s *h, int64_t n);
 cddt_status calc_range_sorted_into(cddt_s *h, const float *pose, float *out, int64_t n, void *scratch,
                                    int64_t scratch_bytes, cudaStream_t st);
+
+// Bump allocation from a caller-owned device buffer (256-byte aligned
+// pieces); take() returns nullptr when the buffer is too small.
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    template <typename T> T *take(size_t n)
+    {
+        const size_t b = (n * sizeof(T) + 255) & ~(size_t)255;
+        if (used + b > cap) return nullptr;
+        T *p = reinterpret_cast<T *>(base + used);
+        used += b;
+        return p;
+    }
+    static size_t need(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+};
 
 // A device buffer freed on scope exit.
 struct Buf {
@@ -71,6 +97,11 @@ struct Segs {
     KT *base;
     const uint32_t *off;
     const uint32_t *len;
+    // when skip_upto > 0, sort_segments leaves alone every segment of at most
+    // skip_upto keys whose companion length (also_len, when given) is at
+    // most skip_upto too
+    const uint32_t *also_len = nullptr;
+    uint32_t skip_upto = 0;
     __device__ __forceinline__ void get(uint32_t id, KT *&p, uint32_t &n) const
     {
         if (hdr) {
@@ -85,7 +116,7 @@ struct Segs {
 
 // Sort every segment ascending (cddt_build.cu).  Synchronises `st`.
 template <typename KT>
-cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st);
+cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st, Arena *ws = nullptr);
 // Fill the trees and headers of every bin from the sorted leaf runs.
 cddt_status index_store(cddt_s *h, cudaStream_t st);
 // Slice tables' eps for pruning: 32 units in the last place of the largest
@@ -99,5 +130,71 @@ inline unsigned grid_cap(int64_t n, int threads, int64_t cap = 152 * 64)
     if (b < 1) b = 1;
     return (unsigned)b;
 }
+
+template <typename KT>
+__device__ __forceinline__ uint32_t key_bits(KT v)
+{
+    if (sizeof(KT) == 4) return __float_as_uint(*reinterpret_cast<const float *>(&v));
+    return (uint32_t)(*reinterpret_cast<const uint16_t *>(&v));
+}
+
+// Index one bin whose sorted keys sit in its leaf run (one warp, all lanes):
+// pad the last leaf, fill the internal levels with the largest key under
+// each child, and write the root separators (or the keys of a small bin) and
+// the tree shape into the header.  The warp's writes of the leaf run must be
+// visible to all its lanes (a __syncwarp after writing them is enough).
+template <typename KT>
+__device__ __forceinline__ void index_bin(void *store, BinHdr *hdr, int64_t g, int lane)
+{
+    constexpr int LK = KeyT<KT>::LK;
+    constexpr int R = KeyT<KT>::R;
+    {
+        const uint32_t n = bin_count(hdr[g].nm), off = hdr[g].off;
+        if (n == 0) return;
+        KT *run = reinterpret_cast<KT *>(store) + ((size_t)off << LK);
+        const uint32_t L0 = ((n - 1) >> LK) + 1;
+        const int h = run_levels(L0, LK, R);
+        const uint32_t internal = internal_nodes(n, LK, R);
+        KT *leaves = run + ((size_t)internal << LK);
+        for (uint32_t i = n + lane; i < (L0 << LK); i += 32) leaves[i] = pad_key<KT>();
+        uint32_t loff = 0;
+        for (int l = h; l >= 1; --l) {
+            const uint32_t cnt = level_count(L0, LK, l);
+            for (uint32_t slot = lane; slot < (cnt << LK); slot += 32) {
+                const uint64_t first = (uint64_t)slot << (LK * l);
+                KT v = pad_key<KT>();
+                if (first < n) {
+                    uint64_t last = ((uint64_t)slot + 1) << (LK * l);
+                    if (last > n) last = n;
+                    v = leaves[last - 1];
+                }
+                run[((size_t)loff << LK) + slot] = v;
+            }
+            loff += cnt;
+        }
+        // header separators: R keys packed into 6 words
+        if (lane < 6) {
+            uint32_t word = 0;
+            const uint32_t cnt_h = level_count(L0, LK, h);
+            const int per = 4 / (int)sizeof(KT);  // keys per word
+            for (int e = 0; e < per; ++e) {
+                const uint32_t q = (uint32_t)(lane * per + e);
+                KT v = pad_key<KT>();
+                if (n <= (uint32_t)R) {
+                    if (q < n) v = leaves[q];
+                } else if (q < cnt_h) {
+                    uint64_t last = ((uint64_t)q + 1) << (LK * (h + 1));
+                    if (last > n) last = n;
+                    v = leaves[last - 1];
+                }
+                word |= key_bits<KT>(v) << (16 * e);
+            }
+            hdr[g].w[lane] = word;
+        }
+        __syncwarp();
+        if (lane == 0) hdr[g].nm = n | ((uint32_t)h << 24) | (level_count(L0, LK, h) << 28);
+    }
+}
+
 
 }  // namespace cddt

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <vector>
 
@@ -243,7 +244,8 @@ __global__ void upd_flip_kernel(const uint32_t *changed, const uint32_t *nchange
 template <typename KT, int PASS>
 __global__ void upd_delta_kernel(const uint32_t *flips, const uint32_t *nflips, int W, const SliceInfo *slices, int S,
                                  float Q, uint32_t *ins_n, uint32_t *del_n, const uint32_t *ins_off,
-                                 const uint32_t *del_off, KT *ins_keys, KT *del_keys)
+                                 const uint32_t *del_off, KT *ins_keys, KT *del_keys, uint32_t *ins_bin,
+                                 uint32_t *del_bin)
 {
     const int64_t total = (int64_t)(*nflips) * S;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -267,8 +269,15 @@ __global__ void upd_delta_kernel(const uint32_t *flips, const uint32_t *nflips, 
                 atomicAdd(ins ? ins_n + g : del_n + g, 1u);
             } else {
                 // ins_n / del_n are cursors here (zeroed before this pass)
-                if (ins) ins_keys[ins_off[g] + atomicAdd(ins_n + g, 1u)] = key;
-                else del_keys[del_off[g] + atomicAdd(del_n + g, 1u)] = key;
+                if (ins) {
+                    const uint32_t t = ins_off[g] + atomicAdd(ins_n + g, 1u);
+                    ins_keys[t] = key;
+                    ins_bin[t] = g;
+                } else {
+                    const uint32_t t = del_off[g] + atomicAdd(del_n + g, 1u);
+                    del_keys[t] = key;
+                    del_bin[t] = g;
+                }
             }
         }
     }
@@ -308,19 +317,110 @@ __device__ __forceinline__ int upper_bound_k(const KT *a, int n, KT v)
     return lo;
 }
 
+// Number of a node's stored keys below v (raw key order), over words
+// [from, 8): one key per word for float32, two for 16-bit keys.
+template <typename KT>
+__device__ __forceinline__ int raw_count_lt(const uint32_t (&w)[8], int from, KT v)
+{
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i < from) continue;
+        if (sizeof(KT) == 4) c += __uint_as_float(w[i]) < *reinterpret_cast<const float *>(&v);
+        else {
+            const uint32_t x = (uint32_t)*reinterpret_cast<const uint16_t *>(&v);
+            c += (w[i] & 0xffffu) < x;
+            c += (w[i] >> 16) < x;
+        }
+    }
+    return c;
+}
+
+// lower_bound (the number of keys below v) in a bin of an indexed store,
+// through its header and tree: one node per level instead of a binary
+// search's log2(n) dependent probes.
+template <typename KT>
+__device__ __forceinline__ int tree_lower_bound(const void *store, const BinHdr &hb, KT v)
+{
+    constexpr int LK = KeyT<KT>::LK;
+    constexpr int K = KeyT<KT>::K;
+    constexpr int R = KeyT<KT>::R;
+    const uint32_t n = bin_count(hb.nm);
+    if (n == 0) return 0;
+    uint32_t w[8] = {hb.off, hb.nm, hb.w[0], hb.w[1], hb.w[2], hb.w[3], hb.w[4], hb.w[5]};
+    int c = raw_count_lt<KT>(w, 2, v);
+    if (n <= (uint32_t)R) return min(c, (int)n);
+    const uint32_t L0 = ((n - 1) >> LK) + 1;
+    const int h = (int)((hb.nm >> 24) & 15u);
+    const int cnt_h = (int)(hb.nm >> 28);
+    if (c >= cnt_h) return (int)n;
+    const char *run = reinterpret_cast<const char *>(store) + ((size_t)hb.off << 5);
+    uint32_t loff = 0, k = (uint32_t)c, cnt = (uint32_t)cnt_h;
+    for (int l = h; l >= 1; --l) {
+        ld_node(run + ((size_t)(loff + k) << 5), w);
+        const int cc = raw_count_lt<KT>(w, 0, v);
+        loff += cnt;
+        cnt = ((L0 - 1) >> (LK * (l - 1))) + 1;
+        k = min(k * K + (uint32_t)cc, cnt - 1);
+    }
+    ld_node(run + ((size_t)(loff + k) << 5), w);
+    return min((int)(k * K) + raw_count_lt<KT>(w, 0, v), (int)n);
+}
+
+__device__ __forceinline__ uint32_t key_word(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint32_t key_word(uint16_t v) { return (uint32_t)v; }
+__device__ __forceinline__ float shfl_key(float v, int k) { return __shfl_sync(0xffffffffu, v, k); }
+__device__ __forceinline__ uint16_t shfl_key(uint16_t v, int k)
+{
+    return (uint16_t)__shfl_sync(0xffffffffu, (uint32_t)v, k);
+}
+
+// After the per-bin sort of the deltas: for every insert, the number of old
+// keys below it (lower_bound in its bin); for every delete, the index of the
+// old key it removes (lower_bound plus its rank among equal deletes of the
+// bin).  One thread per delta, each a tree search of the old store.
+template <typename KT>
+__global__ void upd_locate_kernel(const KT *keys, const uint32_t *bins, const uint32_t *seg_off,
+                                  const uint32_t *seg_len, const uint32_t *also_len, int64_t total, bool deletes,
+                                  const void *old_store, const BinHdr *old_hdr, int32_t *pos, int *status)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = bins[t];
+        const KT key = keys[t];
+        const BinHdr ob = old_hdr[g];
+        int p = tree_lower_bound<KT>(old_store, ob, key);
+        if (deletes) {
+            // rank among the bin's equal deletes (any order of them is fine:
+            // equal deletes remove distinct equal keys)
+            const int64_t first = seg_off[g];
+            if (seg_len[g] > 32 || also_len[g] > 32)  // sorted: equal deletes are adjacent
+                for (int64_t u = t - 1; u >= first && keys[u] == key; --u) ++p;
+            else
+                for (int64_t u = first; u < t; ++u) p += keys[u] == key;
+            const uint32_t n = bin_count(ob.nm);
+            if (p >= (int)n || leaf_run<KT>(const_cast<void *>(old_store), ob.off, n)[p] != key) {
+                flag_error(status);  // a delete with no key to remove
+                p = 0x7fffffff;
+            }
+        }
+        pos[t] = p;
+    }
+}
+
 // Merge each bin's old sorted keys with its sorted inserts, dropping one
 // occurrence per delete.  For an old key v at index i (first occurrence a):
 // it is deleted iff i - a < (#deletes equal to v); a kept key lands at
 // i - #(deletes <= v) + #(inserts <= v).  An insert u at index j lands at
 // j + #(old < u) - #(deletes < u).  (Inserts precede equal old keys.)
 template <typename KT>
-__global__ void upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, void *new_store, const BinHdr *new_hdr,
-                                 const KT *ins_keys, const uint32_t *ins_off, const uint32_t *ins_n, const KT *del_keys,
-                                 const uint32_t *del_off, const uint32_t *del_n, int64_t nbins, int *status)
+__device__ __forceinline__ void merge_bin(const void *old_store, const BinHdr *old_hdr, void *new_store,
+                                          const BinHdr *new_hdr, const KT *ins_keys, const uint32_t *ins_off,
+                                          const uint32_t *ins_n, const KT *del_keys, const uint32_t *del_off,
+                                          const uint32_t *del_n, const int32_t *ins_lb, const int32_t *del_pos,
+                                          int64_t g, int lane, int *status)
 {
-    const int lane = threadIdx.x & 31;
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
-         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    {
         const BinHdr ob = old_hdr[g], nb = new_hdr[g];
         const uint32_t obn = bin_count(ob.nm), nbn = bin_count(nb.nm);
         const KT *old = leaf_run<KT>(const_cast<void *>(old_store), ob.off, obn);
@@ -328,10 +428,96 @@ __global__ void upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, v
         const int n = (int)obn, ni = (int)ins_n[g], nd = (int)min(del_n[g], obn), nn = (int)nbn;
         const KT *I = ins_keys + ins_off[g];
         const KT *Dl = del_keys + del_off[g];
+        // 16-byte pieces: leaf runs are 32-byte aligned and padded to whole
+        // leaves, so a piece that starts below n lies inside the run
+        constexpr int V = 16 / (int)sizeof(KT);
         if (ni == 0 && nd == 0) {
-            for (int i = lane; i < n && i < nn; i += 32) dst[i] = old[i];
-            continue;
+            if (n == nn)
+                for (int i = lane * V; i < n; i += 32 * V)
+                    *reinterpret_cast<uint4 *>(dst + i) = __ldg(reinterpret_cast<const uint4 *>(old + i));
+            else
+                flag_error(status);
+            return;
         }
+        if (ni <= 32 && nd <= 32) {
+            // Few changes (the common case): lane k holds insert k (with the
+            // number of old keys below it) and the old index that delete k
+            // removes.  A kept old key at index i moves to i - #(deletes
+            // placed before i) + #(inserts <= its value), and insert j to
+            // j + #(old < u_j) - #(deletes < u_j) (inserts precede equal old
+            // keys).
+            const KT ik = lane < ni ? I[lane] : KT(0);
+            const int ilb = lane < ni ? ins_lb[ins_off[g] + lane] : 0;
+            const int dpos = lane < nd ? del_pos[del_off[g] + lane] : 0x7fffffff;
+            // each lane takes U 16-byte pieces of V keys per pass (8 keys)
+            constexpr int U = 8 / V > 0 ? 8 / V : 1;
+            for (int i0 = 0; i0 < n; i0 += 32 * V * U) {
+                KT v[U][V];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int ib = i0 + (u * 32 + lane) * V;
+                    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                    if (ib < n) q = __ldg(reinterpret_cast<const uint4 *>(old + ib));
+                    memcpy(v[u], &q, 16);
+                }
+                int dbefore[U][V], ibefore[U][V];
+                bool gone[U][V];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        dbefore[u][e] = 0;
+                        ibefore[u][e] = 0;
+                        gone[u][e] = false;
+                    }
+                for (int k = 0; k < nd; ++k) {
+                    const int pk = __shfl_sync(0xffffffffu, dpos, k);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const int i = i0 + (u * 32 + lane) * V + e;
+                            dbefore[u][e] += pk < i;
+                            gone[u][e] |= pk == i;
+                        }
+                }
+                for (int k = 0; k < ni; ++k) {
+                    const KT uk = shfl_key(ik, k);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int e = 0; e < V; ++e) ibefore[u][e] += !(v[u][e] < uk);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int i = i0 + (u * 32 + lane) * V + e;
+                        if (i < n && !gone[u][e]) {
+                            const int pos = i - dbefore[u][e] + ibefore[u][e];
+                            if (pos < 0 || pos >= nn) flag_error(status);
+                            else dst[pos] = v[u][e];
+                        }
+                    }
+            }
+            // inserts in any order: insert j's rank among the bin's inserts
+            int jr = 0;
+            for (int k = 0; k < ni; ++k) {
+                const KT uk = shfl_key(ik, k);
+                jr += (uk < ik) || (uk == ik && k < lane);
+            }
+            if (lane < ni) {
+                int dlt = 0;  // deletes below the insert
+                for (int k = 0; k < nd; ++k) dlt += Dl[k] < ik;
+                const int pos = jr + ilb - dlt;
+                if (pos < 0 || pos >= nn) flag_error(status);
+                else dst[pos] = ik;
+            }
+            return;
+        }
+        // many changes: binary searches per key.  For an old key v at index i
+        // (first occurrence a): it is deleted iff i - a < (#deletes equal to
+        // v); a kept key lands at i - #(deletes <= v) + #(inserts <= v).
         for (int i = lane; i < n; i += 32) {
             const KT v = old[i];
             const int a = lower_bound_k<KT>(old, n, v);
@@ -356,6 +542,41 @@ __global__ void upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, v
     }
 }
 
+
+// One warp per bin: merge, then index the new run (its keys were just
+// written by this warp and are read back from L2, not HBM).
+template <typename KT>
+__global__ void upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, void *new_store, BinHdr *new_hdr,
+                                 const KT *ins_keys, const uint32_t *ins_off, const uint32_t *ins_n, const KT *del_keys,
+                                 const uint32_t *del_off, const uint32_t *del_n, const int32_t *ins_lb,
+                                 const int32_t *del_pos, int64_t nbins, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
+         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        merge_bin<KT>(old_store, old_hdr, new_store, new_hdr, ins_keys, ins_off, ins_n, del_keys, del_off, del_n,
+                      ins_lb, del_pos, g, lane, status);
+        __syncwarp();
+        index_bin<KT>(new_store, new_hdr, g, lane);
+    }
+}
+
+// Grow-only device buffer of the handle (freed with the handle).
+static cddt_status reserve(void **buf, size_t *have, size_t bytes)
+{
+    if (bytes <= *have) return CDDT_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    const size_t want = bytes + bytes / 4;
+    CDDT_CUDA(cudaMalloc(buf, want));
+    *have = want;
+    return CDDT_OK;
+}
+
+// Online update (Section IV-D, batched): all temporaries live in the
+// handle's workspaces and the new store goes into the buffer the previous
+// update left behind, so a steady stream of updates allocates nothing.
 template <typename KT>
 static cddt_status update_kt(cddt_s *h, const int32_t *xy, const uint8_t *occ, int32_t n, cudaStream_t st)
 {
@@ -372,71 +593,92 @@ static cddt_status update_kt(cddt_s *h, const int32_t *xy, const uint8_t *occ, i
         CDDT_CUDA(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * (size_t)ncell, st));
         h->epoch = 1;
     }
-    Buf changed, flips, counters;
-    CDDT_CUDA(changed.alloc(sizeof(uint32_t) * (size_t)n));
-    CDDT_CUDA(flips.alloc(sizeof(uint32_t) * 9 * (size_t)n));
-    CDDT_CUDA(counters.alloc(sizeof(uint32_t) * 2));
-    CDDT_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(uint32_t) * 2, st));
-    uint32_t *nchanged = counters.as<uint32_t>(), *nflips = nchanged + 1;
+    // workspace: every piece below, sized by n and the bin count
+    const size_t sse = (size_t)scan_scratch_elems(nb);
+    const size_t nbz = (size_t)std::max<int64_t>(nb, 1);
+    size_t bytes = Arena::need(4 * (size_t)n) + Arena::need(36 * (size_t)n) + Arena::need(8) +
+                   Arena::need(20 * nbz) + Arena::need(8 * sse) + Arena::need(16) + Arena::need(8 * nbz) +
+                   Arena::need(sizeof(BinHdr) * nbz) + 2 * (Arena::need(16 * nbz) + Arena::need(16)) +
+                   Arena::need(4 * nbz) + 2 * Arena::need(8 * sse) + Arena::need(24);
+    CDDT_TRY(reserve(&h->ws, &h->ws_bytes, bytes));
+    Arena ws{reinterpret_cast<char *>(h->ws), h->ws_bytes, 0};
+    uint32_t *changed = ws.take<uint32_t>((size_t)n), *flips = ws.take<uint32_t>(9 * (size_t)n);
+    uint32_t *nchanged = ws.take<uint32_t>(2), *nflips = nchanged + 1;
+    uint32_t *arr = ws.take<uint32_t>(5 * nbz);
+    uint64_t *scratch = ws.take<uint64_t>(sse), *tot = ws.take<uint64_t>(2);
+    uint32_t *cur = ws.take<uint32_t>(2 * nbz);
+    BinHdr *old_hdr = ws.take<BinHdr>(nbz);
+    if (!changed || !flips || !nchanged || !arr || !scratch || !tot || !cur || !old_hdr) return CDDT_ERR_OOM;
+    CDDT_CUDA(cudaMemsetAsync(nchanged, 0, sizeof(uint32_t) * 2, st));
     const unsigned gn = grid_cap(n, 256);
     upd_dedupe_kernel<<<gn, 256, 0, st>>>(xy, n, h->W, h->H, h->last_writer, h->status);
-    upd_apply_kernel<<<gn, 256, 0, st>>>(xy, occ, n, h->W, h->H, h->last_writer, h->grid, changed.as<uint32_t>(), nchanged);
-    upd_flip_kernel<<<gn, 256, 0, st>>>(changed.as<uint32_t>(), nchanged, h->W, h->H, h->grid, h->edge, h->stamp,
-                                        h->epoch, flips.as<uint32_t>(), nflips);
+    upd_apply_kernel<<<gn, 256, 0, st>>>(xy, occ, n, h->W, h->H, h->last_writer, h->grid, changed, nchanged);
+    upd_flip_kernel<<<gn, 256, 0, st>>>(changed, nchanged, h->W, h->H, h->grid, h->edge, h->stamp, h->epoch, flips,
+                                        nflips);
     // per-bin insert / delete counts and offsets
-    Buf arr, scratch, tot;
-    CDDT_CUDA(arr.alloc(sizeof(uint32_t) * 5 * (size_t)std::max<int64_t>(nb, 1)));
-    CDDT_CUDA(scratch.alloc(sizeof(uint64_t) * (size_t)scan_scratch_elems(nb)));
-    CDDT_CUDA(tot.alloc(sizeof(uint64_t) * 2));
-    uint32_t *ins_n = arr.as<uint32_t>(), *del_n = ins_n + nb, *ins_off = del_n + nb, *del_off = ins_off + nb,
-             *new_n = del_off + nb;
+    uint32_t *ins_n = arr, *del_n = ins_n + nb, *ins_off = del_n + nb, *del_off = ins_off + nb, *new_n = del_off + nb;
     CDDT_CUDA(cudaMemsetAsync(ins_n, 0, sizeof(uint32_t) * 2 * (size_t)nb, st));
     const unsigned gd = grid_cap((int64_t)9 * n * h->S, 256, 152 * 32);
-    upd_delta_kernel<KT, 0><<<gd, 256, 0, st>>>(flips.as<uint32_t>(), nflips, h->W, h->slices, h->S, h->Q, ins_n, del_n,
-                                                nullptr, nullptr, nullptr, nullptr);
-    exclusive_scan_u32(ins_n, ins_off, nb, scratch.as<uint64_t>(), tot.as<uint64_t>(), st);
-    exclusive_scan_u32(del_n, del_off, nb, scratch.as<uint64_t>(), tot.as<uint64_t>() + 1, st);
+    upd_delta_kernel<KT, 0><<<gd, 256, 0, st>>>(flips, nflips, h->W, h->slices, h->S, h->Q, ins_n, del_n, nullptr,
+                                                nullptr, nullptr, nullptr, nullptr, nullptr);
+    exclusive_scan_u32(ins_n, ins_off, nb, scratch, tot, st);
+    exclusive_scan_u32(del_n, del_off, nb, scratch, tot + 1, st);
     upd_newcount_kernel<<<grid_cap(nb, 256), 256, 0, st>>>(h->hdr, ins_n, del_n, nb, new_n, h->status);
     uint64_t totals[2];
-    CDDT_CUDA(cudaMemcpyAsync(totals, tot.p, sizeof(totals), cudaMemcpyDeviceToHost, st));
+    CDDT_CUDA(cudaMemcpyAsync(totals, tot, sizeof(totals), cudaMemcpyDeviceToHost, st));
     CDDT_CUDA(cudaStreamSynchronize(st));
     CDDT_CUDA(cudaGetLastError());
     if (totals[0] + totals[1] == 0) return CDDT_OK;  // no edge status changed
-    Buf ins_keys, del_keys, cur;
-    CDDT_CUDA(ins_keys.alloc(sizeof(KT) * (size_t)std::max<uint64_t>(totals[0], 1)));
-    CDDT_CUDA(del_keys.alloc(sizeof(KT) * (size_t)std::max<uint64_t>(totals[1], 1)));
-    CDDT_CUDA(cur.alloc(sizeof(uint32_t) * 2 * (size_t)nb));
-    uint32_t *ins_cur = cur.as<uint32_t>(), *del_cur = ins_cur + nb;
-    CDDT_CUDA(cudaMemsetAsync(cur.p, 0, sizeof(uint32_t) * 2 * (size_t)nb, st));
-    upd_delta_kernel<KT, 1><<<gd, 256, 0, st>>>(flips.as<uint32_t>(), nflips, h->W, h->slices, h->S, h->Q, ins_cur, del_cur,
-                                                ins_off, del_off, ins_keys.as<KT>(), del_keys.as<KT>());
-    cddt_status rc = sort_segments<KT>(Segs<KT>{nullptr, nullptr, ins_keys.as<KT>(), ins_off, ins_n}, nb, st);
-    if (rc == CDDT_OK) rc = sort_segments<KT>(Segs<KT>{nullptr, nullptr, del_keys.as<KT>(), del_off, del_n}, nb, st);
+    // per delta: key, bin and (after the sort) its place in the old bin
+    const size_t ni_t = (size_t)std::max<uint64_t>(totals[0], 1), nd_t = (size_t)std::max<uint64_t>(totals[1], 1);
+    const size_t kb = Arena::need(sizeof(KT) * ni_t) + Arena::need(sizeof(KT) * nd_t) + Arena::need(4 * ni_t) +
+                      Arena::need(4 * nd_t) + Arena::need(4 * ni_t) + Arena::need(4 * nd_t);
+    CDDT_TRY(reserve(&h->ws_keys, &h->ws_keys_bytes, kb));
+    Arena wk{reinterpret_cast<char *>(h->ws_keys), h->ws_keys_bytes, 0};
+    KT *ins_keys = wk.take<KT>(ni_t), *del_keys = wk.take<KT>(nd_t);
+    uint32_t *ins_bin = wk.take<uint32_t>(ni_t), *del_bin = wk.take<uint32_t>(nd_t);
+    int32_t *ins_lb = wk.take<int32_t>(ni_t), *del_pos = wk.take<int32_t>(nd_t);
+    uint32_t *ins_cur = cur, *del_cur = cur + nb;
+    CDDT_CUDA(cudaMemsetAsync(cur, 0, sizeof(uint32_t) * 2 * (size_t)nb, st));
+    upd_delta_kernel<KT, 1><<<gd, 256, 0, st>>>(flips, nflips, h->W, h->slices, h->S, h->Q, ins_cur, del_cur, ins_off,
+                                                del_off, ins_keys, del_keys, ins_bin, del_bin);
+    // only bins with more than 32 inserts or deletes need sorted lists (the
+    // merge's binary-search path); the others are merged in any order
+    cddt_status rc =
+        sort_segments<KT>(Segs<KT>{nullptr, nullptr, ins_keys, ins_off, ins_n, del_n, 32}, nb, st, &ws);
+    if (rc == CDDT_OK)
+        rc = sort_segments<KT>(Segs<KT>{nullptr, nullptr, del_keys, del_off, del_n, ins_n, 32}, nb, st, &ws);
     if (rc != CDDT_OK) return rc;
-    // new layout, then the merge from the old store into the new one
-    Buf old_hdr;
-    CDDT_CUDA(old_hdr.alloc(sizeof(BinHdr) * (size_t)nb));
-    CDDT_CUDA(cudaMemcpyAsync(old_hdr.p, h->hdr, sizeof(BinHdr) * nb, cudaMemcpyDeviceToDevice, st));
+    // places of the deltas in the old store, a new layout into the spare
+    // store, then the merge from the old store
+    CDDT_CUDA(cudaMemcpyAsync(old_hdr, h->hdr, sizeof(BinHdr) * nb, cudaMemcpyDeviceToDevice, st));
+    if (totals[0])
+        upd_locate_kernel<KT><<<grid_cap((int64_t)totals[0], 256), 256, 0, st>>>(
+            ins_keys, ins_bin, ins_off, ins_n, del_n, (int64_t)totals[0], false, h->store, old_hdr, ins_lb, h->status);
+    if (totals[1])
+        upd_locate_kernel<KT><<<grid_cap((int64_t)totals[1], 256), 256, 0, st>>>(
+            del_keys, del_bin, del_off, del_n, ins_n, (int64_t)totals[1], true, h->store, old_hdr, del_pos, h->status);
     void *store = nullptr;
     int64_t nodes = 0;
-    rc = layout_bins(h, new_n, st, &store, &nodes, 0);
+    rc = layout_bins(h, new_n, st, &store, &nodes, std::max<int64_t>(h->store_nodes / 8, 1024), &ws, &h->spare,
+                     &h->spare_nodes);
     if (rc != CDDT_OK) {
-        cudaMemcpyAsync(h->hdr, old_hdr.p, sizeof(BinHdr) * nb, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(h->hdr, old_hdr, sizeof(BinHdr) * nb, cudaMemcpyDeviceToDevice, st);
         cudaStreamSynchronize(st);
         return rc;
     }
-    upd_merge_kernel<KT><<<grid_cap(nb * 32, 256), 256, 0, st>>>(h->store, old_hdr.as<BinHdr>(), store, h->hdr, ins_keys.as<KT>(),
-                                                                 ins_off, ins_n, del_keys.as<KT>(), del_off, del_n, nb,
+    const int64_t store_cap = h->spare_nodes;
+    upd_merge_kernel<KT><<<grid_cap(nb * 32, 256), 256, 0, st>>>(h->store, old_hdr, store, h->hdr, ins_keys, ins_off,
+                                                                 ins_n, del_keys, del_off, del_n, ins_lb, del_pos, nb,
                                                                  h->status);
     CDDT_CUDA(cudaGetLastError());
-    CDDT_CUDA(cudaStreamSynchronize(st));
-    cudaFree(h->store);
+    // the old store becomes the next update's target (stream order keeps the
+    // merge's reads of it before any later write)
+    h->spare = h->store;
+    h->spare_nodes = h->store_cap;
     h->store = store;
     h->store_nodes = nodes;
-    h->store_cap = std::max<int64_t>(nodes, 1);
-    rc = index_store(h, st);
-    if (rc != CDDT_OK) return rc;
-    CDDT_CUDA(cudaStreamSynchronize(st));
+    h->store_cap = store_cap;
     return CDDT_OK;
 }
 

@@ -130,6 +130,30 @@ def test_update_sequence_equals_rebuild(G, oracle, u16):
     assert d.stats()["update_ms"] > 0
 
 
+@pytest.mark.parametrize("u16", [False, True])
+def test_update_bin_with_many_deltas(G, oracle, u16):
+    """A wall of 300 cells written along one row, then half of it cleared:
+    the row's bins get hundreds of inserts and deletes (the merge's sorted
+    path), while other bins get a handful (its unsorted path)."""
+    g = np.zeros((64, 512), np.uint8)
+    g[0, :] = g[-1, :] = 1
+    g[:, 0] = g[:, -1] = 1
+    N, mr = 40, 600.0
+    d = G.CDDT(dev(g), N, mr, u16=u16)
+    cur = g.copy()
+    wall = np.array([(x, 30) for x in range(100, 400)], np.int32)
+    for xy, occ in ((wall, np.ones(len(wall), np.uint8)), (wall[::2], np.zeros(len(wall[::2]), np.uint8)),
+                    (np.array([[5, 5], [6, 5], [7, 9]], np.int32), np.ones(3, np.uint8))):
+        d.update_cells(dev(xy), dev(occ))
+        assert d.status() == G.CDDT_OK
+        for (x, y), v in zip(xy, occ):
+            cur[y, x] = v
+        same_store(d, oracle.OracleCDDT(cur, N, mr, u16=u16))
+    q = gc.random_queries(512, 64, 20000, 6)
+    ref = oracle.OracleCDDT(cur, N, mr, u16=u16)
+    assert bits_equal(d.calc_range_many(dev(q)).cpu().numpy(), ref.calc_range(q))
+
+
 def test_update_repeated_cells_last_write_wins(G, oracle):
     g = synth.rect_map(64, 64, n_rects=6, seed=5)
     d = G.CDDT(dev(g), 24, 100.0)
