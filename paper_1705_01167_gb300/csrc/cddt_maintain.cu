@@ -515,29 +515,80 @@ __device__ __forceinline__ void merge_bin(const void *old_store, const BinHdr *o
             }
             return;
         }
-        // many changes: binary searches per key.  For an old key v at index i
-        // (first occurrence a): it is deleted iff i - a < (#deletes equal to
-        // v); a kept key lands at i - #(deletes <= v) + #(inserts <= v).
-        for (int i = lane; i < n; i += 32) {
-            const KT v = old[i];
-            const int a = lower_bound_k<KT>(old, n, v);
-            const int r_lt = lower_bound_k<KT>(Dl, nd, v), r_le = upper_bound_k<KT>(Dl, nd, v);
-            if (i - a < r_le - r_lt) continue;
-            const int pos = i - r_le + upper_bound_k<KT>(I, ni, v);
-            if (pos < 0 || pos >= nn) {
-                flag_error(status);
-                continue;
+        // Many changes (inserts and deletes sorted, delete positions
+        // ascending): the run is streamed in chunks like above, and each chunk
+        // counts only the deletes placed inside it and the inserts between its
+        // first and last key; everything before the chunk is a base count.
+        const int32_t *DP = del_pos + del_off[g];
+        const int32_t *IL = ins_lb + ins_off[g];
+        constexpr int U = 8 / V > 0 ? 8 / V : 1;
+        constexpr int C = 32 * V * U;  // keys per chunk
+        for (int i0 = 0; i0 < n; i0 += C) {
+            const int iend = min(i0 + C, n);
+            const int d_lo = lower_bound_k<int32_t>(DP, nd, i0), d_hi = lower_bound_k<int32_t>(DP, nd, iend);
+            const int i_lo = lower_bound_k<KT>(I, ni, old[i0]), i_hi = upper_bound_k<KT>(I, ni, old[iend - 1]);
+            KT v[U][V];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int ib = i0 + (u * 32 + lane) * V;
+                uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                if (ib < n) q = __ldg(reinterpret_cast<const uint4 *>(old + ib));
+                memcpy(v[u], &q, 16);
             }
-            dst[pos] = v;
+            int dbefore[U][V], ibefore[U][V];
+            bool gone[U][V];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    dbefore[u][e] = d_lo;
+                    ibefore[u][e] = i_lo;
+                    gone[u][e] = false;
+                }
+            for (int b = d_lo; b < d_hi; b += 32) {
+                const int pl = b + lane < d_hi ? DP[b + lane] : 0x7fffffff;
+                const int m = min(32, d_hi - b);
+                for (int k = 0; k < m; ++k) {
+                    const int pk = __shfl_sync(0xffffffffu, pl, k);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const int i = i0 + (u * 32 + lane) * V + e;
+                            dbefore[u][e] += pk < i;
+                            gone[u][e] |= pk == i;
+                        }
+                }
+            }
+            for (int b = i_lo; b < i_hi; b += 32) {
+                const KT ul = b + lane < i_hi ? I[b + lane] : KT(0);
+                const int m = min(32, i_hi - b);
+                for (int k = 0; k < m; ++k) {
+                    const KT uk = shfl_key(ul, k);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int e = 0; e < V; ++e) ibefore[u][e] += !(v[u][e] < uk);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const int i = i0 + (u * 32 + lane) * V + e;
+                    if (i < n && !gone[u][e]) {
+                        const int pos = i - dbefore[u][e] + ibefore[u][e];
+                        if (pos < 0 || pos >= nn) flag_error(status);
+                        else dst[pos] = v[u][e];
+                    }
+                }
         }
+        // insert j lands at j + #(old < u_j) - #(deletes < u_j)
         for (int j = lane; j < ni; j += 32) {
             const KT u = I[j];
-            const int pos = j + lower_bound_k<KT>(old, n, u) - lower_bound_k<KT>(Dl, nd, u);
-            if (pos < 0 || pos >= nn) {
-                flag_error(status);
-                continue;
-            }
-            dst[pos] = u;
+            const int pos = j + IL[j] - lower_bound_k<KT>(Dl, nd, u);
+            if (pos < 0 || pos >= nn) flag_error(status);
+            else dst[pos] = u;
         }
     }
 }
@@ -546,7 +597,7 @@ __device__ __forceinline__ void merge_bin(const void *old_store, const BinHdr *o
 // One warp per bin: merge, then index the new run (its keys were just
 // written by this warp and are read back from L2, not HBM).
 template <typename KT>
-__global__ void upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, void *new_store, BinHdr *new_hdr,
+__global__ void __launch_bounds__(256, 4) upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, void *new_store, BinHdr *new_hdr,
                                  const KT *ins_keys, const uint32_t *ins_off, const uint32_t *ins_n, const KT *del_keys,
                                  const uint32_t *del_off, const uint32_t *del_n, const int32_t *ins_lb,
                                  const int32_t *del_pos, int64_t nbins, int *status)
