@@ -268,10 +268,14 @@ static unsigned grid_for(int64_t n, int threads)
 // ------------------------------------------------------------ segmented sort
 
 
-// Size classes of the segmented sort.
+// Size classes of the segmented sort: one lane per key, one warp with up to
+// 16 keys per lane in registers, a block in shared memory (two sizes), and
+// global memory above.
 constexpr uint32_t kWarpSortMax = 32;
+constexpr uint32_t kRegSortMax = 512;
 constexpr uint32_t kBlockSortMax = 2048;
 constexpr uint32_t kBigSortMax = 16384;
+constexpr int kSortClasses = 5;
 
 template <typename KT>
 __global__ void classify_kernel(Segs<KT> sg, int64_t nseg, uint32_t *lists, uint32_t *list_n, int64_t cap)
@@ -292,11 +296,12 @@ __global__ void classify_kernel(Segs<KT> sg, int64_t nseg, uint32_t *lists, uint
                               (!sg.also_len || sg.also_len[g] <= sg.skip_upto);
             if (n <= 1 || skip) cls = -1;
             else if (n <= kWarpSortMax) cls = 0;
+            else if (n <= kRegSortMax) cls = 4;
             else if (n <= kBlockSortMax) cls = 1;
             else if (n <= kBigSortMax) cls = 2;
             else cls = 3;
         }
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < kSortClasses; ++c) {
             const unsigned mine = __ballot_sync(0xffffffffu, cls == c);
             if (!mine) continue;
             uint32_t base = 0;
@@ -344,6 +349,72 @@ __global__ void warp_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t cou
         KT v = lane < (int)n ? run[lane] : pad_key<KT>();
         v = warp_bitonic<KT>(v);
         if (lane < (int)n) run[lane] = v;
+    }
+}
+
+// Ascending bitonic sort of 32 M keys held by one warp, M per lane: key
+// index i = e * 32 + lane.  Partners at distance >= 32 are in the same lane
+// (registers), nearer ones one shuffle away; no barriers.
+template <typename KT, int M>
+__device__ __forceinline__ void warp_reg_sort(KT *run, int n, int lane)
+{
+    constexpr int N = 32 * M;
+    KT r[M];
+#pragma unroll
+    for (int e = 0; e < M; ++e) {
+        const int i = e * 32 + lane;
+        r[e] = i < n ? run[i] : pad_key<KT>();
+    }
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int e = 0; e < M; ++e) {
+                    const int pe = e ^ (j >> 5);
+                    if (pe > e) {
+                        const bool up = (((e * 32 + lane) & k) == 0);
+                        const KT a = r[e], b = r[pe];
+                        const bool sw = up ? (b < a) : (a < b);
+                        r[e] = sw ? b : a;
+                        r[pe] = sw ? a : b;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < M; ++e) {
+                    const KT o = shfl_xor_key(r[e], j);
+                    const bool up = (((e * 32 + lane) & k) == 0);
+                    const bool lower = ((lane & j) == 0);
+                    const KT mn = r[e] < o ? r[e] : o, mx = r[e] < o ? o : r[e];
+                    r[e] = (lower == up) ? mn : mx;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < M; ++e) {
+        const int i = e * 32 + lane;
+        if (i < n) run[i] = r[e];
+    }
+}
+
+// Segments of 33..512 keys: one warp each, the register width picked per
+// segment (warp-uniform).
+template <typename KT>
+__global__ void reg_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t count)
+{
+    const int lane = threadIdx.x & 31;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count;
+         w += (gridDim.x * blockDim.x) >> 5) {
+        KT *run;
+        uint32_t n;
+        sg.get(list[w], run, n);
+        if (n <= 64) warp_reg_sort<KT, 2>(run, (int)n, lane);
+        else if (n <= 128) warp_reg_sort<KT, 4>(run, (int)n, lane);
+        else if (n <= 256) warp_reg_sort<KT, 8>(run, (int)n, lane);
+        else warp_reg_sort<KT, 16>(run, (int)n, lane);
     }
 }
 
@@ -442,19 +513,20 @@ cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st, Are
 {
     if (nseg == 0) return CDDT_OK;
     Buf lists_b, list_n_b;
-    uint32_t *L = ws ? ws->take<uint32_t>(4 * (size_t)nseg) : nullptr;
-    uint32_t *LN = ws ? ws->take<uint32_t>(4) : nullptr;
+    uint32_t *L = ws ? ws->take<uint32_t>(kSortClasses * (size_t)nseg) : nullptr;
+    uint32_t *LN = ws ? ws->take<uint32_t>(kSortClasses) : nullptr;
     if (!L || !LN) {
-        CDDT_CUDA(lists_b.alloc(sizeof(uint32_t) * 4 * (size_t)nseg));
-        CDDT_CUDA(list_n_b.alloc(sizeof(uint32_t) * 4));
+        CDDT_CUDA(lists_b.alloc(sizeof(uint32_t) * kSortClasses * (size_t)nseg));
+        CDDT_CUDA(list_n_b.alloc(sizeof(uint32_t) * kSortClasses));
         L = lists_b.as<uint32_t>();
         LN = list_n_b.as<uint32_t>();
     }
-    CDDT_CUDA(cudaMemsetAsync(LN, 0, sizeof(uint32_t) * 4, st));
+    CDDT_CUDA(cudaMemsetAsync(LN, 0, sizeof(uint32_t) * kSortClasses, st));
     classify_kernel<KT><<<grid_for(nseg, 256), 256, 0, st>>>(sg, nseg, L, LN, nseg);
-    uint32_t cnt[4];
+    uint32_t cnt[kSortClasses];
     CDDT_CUDA(cudaMemcpyAsync(cnt, LN, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CDDT_CUDA(cudaStreamSynchronize(st));
+    if (cnt[4]) reg_sort_kernel<KT><<<grid_for((int64_t)cnt[4] * 32, 256), 256, 0, st>>>(sg, L + 4 * nseg, cnt[4]);
     if (cnt[0]) warp_sort_kernel<KT><<<grid_for((int64_t)cnt[0] * 32, 256), 256, 0, st>>>(sg, L, cnt[0]);
     if (cnt[1]) {
         size_t sm = sizeof(KT) * kBlockSortMax;

@@ -649,7 +649,7 @@ static cddt_status update_kt(cddt_s *h, const int32_t *xy, const uint8_t *occ, i
     const size_t nbz = (size_t)std::max<int64_t>(nb, 1);
     size_t bytes = Arena::need(4 * (size_t)n) + Arena::need(36 * (size_t)n) + Arena::need(8) +
                    Arena::need(20 * nbz) + Arena::need(8 * sse) + Arena::need(16) + Arena::need(8 * nbz) +
-                   Arena::need(sizeof(BinHdr) * nbz) + 2 * (Arena::need(16 * nbz) + Arena::need(16)) +
+                   Arena::need(sizeof(BinHdr) * nbz) + 2 * (Arena::need(4 * 8 * nbz) + Arena::need(4 * 8)) +
                    Arena::need(4 * nbz) + 2 * Arena::need(8 * sse) + Arena::need(24);
     CDDT_TRY(reserve(&h->ws, &h->ws_bytes, bytes));
     Arena ws{reinterpret_cast<char *>(h->ws), h->ws_bytes, 0};
