@@ -269,10 +269,10 @@ static unsigned grid_for(int64_t n, int threads)
 
 
 // Size classes of the segmented sort: one lane per key, one warp with up to
-// 16 keys per lane in registers, a block in shared memory (two sizes), and
-// global memory above.
+// 32 keys per lane in registers, a block with 16 keys per thread in registers
+// (two sizes), and global memory above.
 constexpr uint32_t kWarpSortMax = 32;
-constexpr uint32_t kRegSortMax = 512;
+constexpr uint32_t kRegSortMax = 1024;
 constexpr uint32_t kBlockSortMax = 2048;
 constexpr uint32_t kBigSortMax = 16384;
 constexpr int kSortClasses = 5;
@@ -400,7 +400,7 @@ __device__ __forceinline__ void warp_reg_sort(KT *run, int n, int lane)
     }
 }
 
-// Segments of 33..512 keys: one warp each, the register width picked per
+// Segments of 33..1024 keys: one warp each, the register width picked per
 // segment (warp-uniform).
 template <typename KT>
 __global__ void reg_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t count)
@@ -414,39 +414,101 @@ __global__ void reg_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t coun
         if (n <= 64) warp_reg_sort<KT, 2>(run, (int)n, lane);
         else if (n <= 128) warp_reg_sort<KT, 4>(run, (int)n, lane);
         else if (n <= 256) warp_reg_sort<KT, 8>(run, (int)n, lane);
-        else warp_reg_sort<KT, 16>(run, (int)n, lane);
+        else if (n <= 512) warp_reg_sort<KT, 16>(run, (int)n, lane);
+        else warp_reg_sort<KT, 32>(run, (int)n, lane);
     }
 }
 
-// Block bitonic sort in shared memory, padded to a power of two with +inf.
-template <typename KT>
-__global__ void block_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t count)
+// One register stage of distance J < 16 (keys i = t * 16 + e).
+template <typename KT, int J>
+__device__ __forceinline__ void reg_stage(KT (&r)[16], uint32_t t, uint32_t k)
+{
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int pe = e ^ J;
+        if (pe > e) {
+            const bool up = ((t * 16 + e) & k) == 0;
+            const KT a = r[e], b = r[pe];
+            const bool sw = up ? (b < a) : (a < b);
+            r[e] = sw ? b : a;
+            r[pe] = sw ? a : b;
+        }
+    }
+}
+
+// Segments of 1025..16384 keys: the bitonic network over a power-of-two
+// padded copy with thread t holding keys t * 16 .. t * 16 + 15 in registers.
+// Distances below 16 are register swaps, 16..256 one shuffle, and only the
+// stages of distance >= 512 (across warps) go through shared memory: 15 of
+// the 105 stages for 16384 keys.  Threads past the padded size work on pads
+// among themselves (i ^ j stays above the size).
+template <typename KT, int THREADS>
+__global__ void __launch_bounds__(THREADS) block_reg_sort_kernel(Segs<KT> sg, const uint32_t *list, uint32_t count)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     KT *sh = reinterpret_cast<KT *>(smem_raw);
+    const uint32_t t = threadIdx.x;
+    const int lane = (int)(t & 31);
     for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
         KT *run;
         uint32_t n;
         sg.get(list[w], run, n);
-        uint32_t P = 1;
+        uint32_t P = 512;
         while (P < n) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < n ? run[i] : pad_key<KT>();
-        __syncthreads();
+        const bool act = t * 16 < P;  // whole warps: P is a multiple of 512
+        KT r[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const uint32_t i = t * 16 + e;
+            r[e] = i < n ? run[i] : pad_key<KT>();
+        }
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                    uint32_t p = i ^ j;
-                    if (p > i) {
-                        KT a = sh[i], b = sh[p];
-                        bool up = (i & k) == 0;
-                        if ((a > b) == up) { sh[i] = b; sh[p] = a; }
+                if (j >= 512) {
+                    if (act) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) sh[t * 16 + e] = r[e];
                     }
+                    __syncthreads();
+                    if (act) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const uint32_t i = t * 16 + e;
+                            const KT o = sh[i ^ j];
+                            const bool up = (i & k) == 0, lower = (i & j) == 0;
+                            const KT mn = r[e] < o ? r[e] : o, mx = r[e] < o ? o : r[e];
+                            r[e] = (lower == up) ? mn : mx;
+                        }
+                    }
+                    __syncthreads();
+                } else if (!act) {
+                    // past the padded size: nothing to do between barriers
+                } else if (j >= 16) {
+                    const int d = (int)(j >> 4);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const uint32_t i = t * 16 + e;
+                        const KT o = shfl_xor_key(r[e], d);
+                        const bool up = (i & k) == 0, lower = (lane & d) == 0;
+                        const KT mn = r[e] < o ? r[e] : o, mx = r[e] < o ? o : r[e];
+                        r[e] = (lower == up) ? mn : mx;
+                    }
+                } else if (j == 8) {
+                    reg_stage<KT, 8>(r, t, k);
+                } else if (j == 4) {
+                    reg_stage<KT, 4>(r, t, k);
+                } else if (j == 2) {
+                    reg_stage<KT, 2>(r, t, k);
+                } else {
+                    reg_stage<KT, 1>(r, t, k);
                 }
-                __syncthreads();
             }
         }
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) run[i] = sh[i];
-        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const uint32_t i = t * 16 + e;
+            if (i < n) run[i] = r[e];
+        }
     }
 }
 
@@ -528,14 +590,17 @@ cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st, Are
     CDDT_CUDA(cudaStreamSynchronize(st));
     if (cnt[4]) reg_sort_kernel<KT><<<grid_for((int64_t)cnt[4] * 32, 256), 256, 0, st>>>(sg, L + 4 * nseg, cnt[4]);
     if (cnt[0]) warp_sort_kernel<KT><<<grid_for((int64_t)cnt[0] * 32, 256), 256, 0, st>>>(sg, L, cnt[0]);
-    if (cnt[1]) {
-        size_t sm = sizeof(KT) * kBlockSortMax;
-        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[1], 152 * 8), 256, sm, st>>>(sg, L + nseg, cnt[1]);
+    if (cnt[1]) {  // 1025..2048 keys: 128 threads x 16 keys
+        const size_t sm = sizeof(KT) * kBlockSortMax;
+        block_reg_sort_kernel<KT, kBlockSortMax / 16><<<std::min<uint32_t>(cnt[1], 152 * 16), kBlockSortMax / 16, sm, st>>>(
+            sg, L + nseg, cnt[1]);
     }
-    if (cnt[2]) {
-        size_t sm = sizeof(KT) * kBigSortMax;
-        CDDT_CUDA(cudaFuncSetAttribute(block_sort_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        block_sort_kernel<KT><<<std::min<uint32_t>(cnt[2], 152 * 2), 1024, sm, st>>>(sg, L + 2 * nseg, cnt[2]);
+    if (cnt[2]) {  // 2049..16384 keys: 1024 threads x 16 keys
+        const size_t sm = sizeof(KT) * kBigSortMax;
+        CDDT_CUDA(cudaFuncSetAttribute(block_reg_sort_kernel<KT, kBigSortMax / 16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        block_reg_sort_kernel<KT, kBigSortMax / 16><<<std::min<uint32_t>(cnt[2], 152 * 2), kBigSortMax / 16, sm, st>>>(
+            sg, L + 2 * nseg, cnt[2]);
     }
     if (cnt[3]) {
         Buf dptr, dlen;
