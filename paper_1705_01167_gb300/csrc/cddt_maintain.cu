@@ -35,6 +35,14 @@ float prune_eps(int W, int H)
 
 // ------------------------------------------------------------ prune
 
+// A stored key as the raw word the node comparisons take.
+template <typename KT>
+__device__ __forceinline__ uint32_t raw_key(const KT *leaves, int i)
+{
+    if (sizeof(KT) == 4) return __float_as_uint(__ldg(reinterpret_cast<const float *>(leaves) + i));
+    return (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(leaves) + i);
+}
+
 template <typename KT>
 __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep)
 {
@@ -69,8 +77,18 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep)
             const uint32_t bn = bin_count(bh.nm);
             if (bn == 0) continue;
             int kb;
-            const int l = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, si.X, pol, kb).idx;  // first key >= xlo
-            const int u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, si.X, pol, kb).idx;   // first key > xhi
+            const SearchResult sl = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, si.X, pol, kb);
+            const int l = sl.idx;  // first key >= xlo
+            // first key > xhi: the cell's x' extent is under two units wide,
+            // so it is usually within a few keys of l (the leaf just read)
+            const KT *leaves = leaf_run<KT>(const_cast<void *>(m.store), bh.off, bn);
+            const Cmp<KT, true> above(m, xhi, si.X);
+            int u = l;
+            if (u < (int)bn && above.le(raw_key<KT>(leaves, u))) {
+                ++u;
+                while (u < (int)bn && u < l + 8 && above.le(raw_key<KT>(leaves, u))) ++u;
+                if (u == l + 8) u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, si.X, pol, kb).idx;
+            }
             const int m0 = max(l - 1, 0), m1 = min(u, (int)bn - 1);
             uint8_t *kp = keep + (((size_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK);
             for (int mm = m0; mm <= m1; ++mm) kp[mm] = 1;
