@@ -546,9 +546,29 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_update(args):
+    """A short run for ncu: build the 4000 x 4000 corridor CDDT, then apply
+    warmup + steps batches of 10^4 cell writes (the update4000 writes)."""
+    import torch
+    from paper_1705_01167_gb300 import cddt as G
+    w = WL.update4000(steps=args.warmup + args.steps)
+    dev = torch.device("cuda", 0)
+    d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], w["max_range"])
+    ms = []
+    for xy, occ in w["writes"]:
+        d.update_cells(torch.from_numpy(xy).to(dev), torch.from_numpy(occ).to(dev))
+        ms.append(round(d.stats()["update_ms"], 3))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "update", "update_ms": ms, "status": d.status(),
+                      "zero_points": d.stats()["n_zero_points"]}))
+    return 0
+
+
 def run_profile(args):
     """A short run for ncu: the batched launch (fixed shape), one per-filter
     pass and one sweep launch, a few launches each."""
+    if args.profile_case == "update":
+        return run_profile_update(args)
     import torch
     from paper_1705_01167_gb300 import cddt as G
     w = WL.corridor2000()
@@ -587,6 +607,8 @@ def main():
     ap.add_argument("--workload", default="corridor2000", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
+    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "update"],
+                    help="--profile workload: the corridor plan, or 10^4-write updates on the 4000^2 map")
     ap.add_argument("--shape-tpp", type=int, default=1)
     ap.add_argument("--shape-ppi", type=int, default=512)
     ap.add_argument("--shape-block", type=int, default=512)
