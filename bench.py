@@ -483,11 +483,28 @@ def bench_diff(args, G, torch, dev, world, rank):
     rays = sum(p.shape[0] * bo.numel() for p, bo, _, _ in scans) * (w["refine_steps"] + 1)
     fwd = timed(lambda: [d.sensor_weights(p, bo, obs, m, D) for p, bo, obs, D in scans], args.steps, 2)
     rays_fwd = sum(p.shape[0] * bo.numel() for p, bo, _, _ in scans)
+    # the same step captured once in a CUDA graph (the library's calls are
+    # stream-ordered and allocate nothing), replayed
+    graph_rays = None
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        ms_g = timed(graph.replay, args.steps, 2)
+        graph_rays = rays / (statistics.mean(ms_g) * 1e-3)
+    except RuntimeError as e:
+        print(f"graph capture of the refinement step failed: {e}", file=sys.stderr)
     line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "diff2000",
                      {"launch": "cddt_sensor_weights_fwd_bwd per refinement step (value counts forward+adjoint "
                                 "ray casts)"})
     line.update({"gpu_launches": args.steps * 2 * (w["refine_steps"] + 1),
-                 "forward_only_rays_per_s": rays_fwd / (statistics.mean(fwd) * 1e-3)})
+                 "forward_only_rays_per_s": rays_fwd / (statistics.mean(fwd) * 1e-3),
+                 "graph_rays_per_s": graph_rays})
     return line
 
 
