@@ -283,6 +283,25 @@ CDDT_API cddt_status cddt_get_status(cddt_t h);
 CDDT_API cddt_status cddt_export(cddt_t h, int64_t *slice_base_host, int64_t *bin_start_host,
                         float *zp_host);
 
+/* Checkpoint restore (no counterpart in the paper, which rebuilds a CDDT
+ * instead): a new handle for the grid and parameters given, its store taken
+ * from a CSR that cddt_export wrote for a handle with the same grid,
+ * theta_disc, max_range and flags, instead of being constructed.  total_bins
+ * is that handle's bin count (cddt_stats.total_bins; it must match the
+ * parameters), bin_start_host int64 [total_bins + 1] and zp_host float
+ * [bin_start_host[total_bins]] as cddt_export wrote them (each bin sorted
+ * ascending; for CDDT_ZP_U16 the dequantised values, which re-quantise
+ * exactly).  pruned != 0 marks a store exported from a pruned handle (updates
+ * are then rejected, as on the original).  The host arrays are copied before
+ * the call returns (it synchronises `stream`).  A CSR from another grid gives
+ * a handle whose answers are not those of a build (no memory is accessed out
+ * of bounds).  Errors: ARG (bad arguments, a bin count that does not match
+ * the parameters, an unsorted bin), OOM, CUDA. */
+CDDT_API cddt_status cddt_import(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t theta_disc,
+                                 float max_range, uint32_t flags, int32_t pruned, int64_t total_bins,
+                                 const int64_t *bin_start_host, const float *zp_host, void *stream,
+                                 cddt_t *out);
+
 /* Copy the handle's occupancy grid and edge map (uint8 [H][W]) to the host.
  * Either pointer may be NULL.  Synchronises the device.  Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_export_grid(cddt_t h, uint8_t *grid_host, uint8_t *edge_host);

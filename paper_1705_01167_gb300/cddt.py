@@ -30,6 +30,7 @@ EXPORTED = (
     "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
+    "cddt_import",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -112,6 +113,7 @@ def load(build_if_missing: bool = True):
             "cddt_get_stats": (st, [vp, C.POINTER(Stats)]),
             "cddt_get_status": (st, [vp]),
             "cddt_export": (st, [vp, vp, vp, vp]),
+            "cddt_import": (st, [vp, i32, i32, i32, f32, u32, i32, i64, vp, vp, vp, C.POINTER(vp)]),
             "cddt_export_grid": (st, [vp, vp, vp]),
             "cddt_sensor_work": (st, [vp, vp, i64, vp, i32, i32, vp, vp]),
             "cddt_status_string": (C.c_char_p, [st]),
@@ -193,6 +195,36 @@ class CDDT:
                               CDDT_ZP_U16 if u16 else 0, _stream(stream), C.byref(h))
         _check(rc, "cddt_build")
         self._h = h
+
+    @classmethod
+    def from_export(cls, grid: torch.Tensor, theta_disc: int, max_range: float, bin_start, zp,
+                    u16: bool = False, pruned: bool = False, stream=None) -> "CDDT":
+        """``cddt_import``: a handle whose store is the CSR ``(bin_start, zp)``
+        that ``export()`` returned for the same grid and parameters."""
+        import numpy as np
+        L = load()
+        _dev(grid, torch.uint8, "grid")
+        if grid.dim() != 2:
+            raise ValueError("grid must be [H, W]")
+        bs = np.ascontiguousarray(bin_start, np.int64)
+        z = np.ascontiguousarray(zp, np.float32)
+        if bs.ndim != 1 or bs.size < 1 or z.size < bs[-1]:
+            raise ValueError("bin_start must be [bins + 1] and zp hold bin_start[-1] values")
+        self = cls.__new__(cls)
+        self.H, self.W = grid.shape
+        self.theta_disc = int(theta_disc)
+        self.max_range = float(max_range)
+        self.u16 = bool(u16)
+        self.device = grid.device
+        h = C.c_void_p()
+        with torch.cuda.device(grid.device):
+            rc = L.cddt_import(_ptr(grid), self.W, self.H, self.theta_disc, self.max_range,
+                               CDDT_ZP_U16 if u16 else 0, int(bool(pruned)), bs.size - 1,
+                               bs.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p) if z.size else None,
+                               _stream(stream), C.byref(h))
+        _check(rc, "cddt_import")
+        self._h = h
+        return self
 
     @property
     def handle(self):

@@ -119,6 +119,47 @@ cddt_status cddt_build(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t th
     return CDDT_OK;
 }
 
+cddt_status cddt_import(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t theta_disc, float max_range,
+                        uint32_t flags, int32_t pruned, int64_t total_bins, const int64_t *bin_start_host,
+                        const float *zp_host, void *stream, cddt_t *out)
+{
+    if (!out) return CDDT_ERR_ARG;
+    *out = nullptr;
+    if (!grid_dev || W < 1 || H < 1 || W > 32767 || H > 32767) return CDDT_ERR_ARG;
+    if (theta_disc < 2 || (theta_disc & 1) || theta_disc > 65536) return CDDT_ERR_ARG;
+    if (!(max_range > 0) || !std::isfinite(max_range)) return CDDT_ERR_ARG;
+    if (flags & ~CDDT_ZP_U16) return CDDT_ERR_ARG;
+    if (total_bins < 0 || !bin_start_host) return CDDT_ERR_ARG;
+    if (bin_start_host[total_bins] > 0 && !zp_host) return CDDT_ERR_ARG;
+    if (!device_ok()) return CDDT_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    cddt_s *h = new cddt_s();
+    cudaGetDevice(&h->device);
+    h->W = W;
+    h->H = H;
+    h->N = theta_disc;
+    h->S = theta_disc / 2;
+    h->max_range = max_range;
+    h->flags = flags;
+    h->u16 = (flags & CDDT_ZP_U16) ? 1 : 0;
+    h->pruned = pruned ? 1 : 0;
+    cddt_status rc = cddt::init_handle(h, grid_dev, st, false);
+    if (rc == CDDT_OK && h->total_bins != total_bins) rc = CDDT_ERR_ARG;  // exported with other parameters
+    if (rc == CDDT_OK) rc = cddt::import_store(h, bin_start_host, zp_host, st);
+    if (rc == CDDT_OK) {
+        int flag = 0;
+        if (cudaMemcpy(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = CDDT_ERR_CUDA;
+        else if (flag) rc = CDDT_ERR_ARG;  // a bin of the CSR was not sorted
+    }
+    if (rc != CDDT_OK) {
+        cudaStreamSynchronize(st);
+        free_handle(h);
+        return rc;
+    }
+    *out = h;
+    return CDDT_OK;
+}
+
 cddt_status cddt_destroy(cddt_t h)
 {
     if (!h) return CDDT_OK;

@@ -814,7 +814,7 @@ cddt_status construct(cddt_s *h, cudaStream_t st)
     return CDDT_OK;
 }
 
-cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st)
+cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st, bool build)
 {
     std::vector<SliceInfo> tab;
     slice_tables(h, tab);
@@ -839,7 +839,80 @@ cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st)
     normalise_grid_kernel<<<grid_for(ncell, 256), 256, 0, st>>>(grid_dev, h->grid, ncell);
     edge_map_kernel<<<grid_for(ncell, 256), 256, 0, st>>>(h->grid, h->edge, h->W, h->H);
     CDDT_CUDA(cudaGetLastError());
-    return construct(h, st);
+    return build ? construct(h, st) : CDDT_OK;
+}
+
+// One warp per bin: its keys from an exported CSR into its leaf run (16-bit
+// keys re-quantised, which restores them exactly); a bin that is not sorted
+// ascending flags CDDT_ERR_DEVICE.
+template <typename KT>
+__global__ void load_bins_kernel(const float *zp, const uint32_t *start, const float *bin_X, const BinHdr *hdr,
+                                 void *store, int64_t nbins, float Q, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
+         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t n = bin_count(hdr[g].nm);
+        if (n == 0) continue;
+        KT *run = leaf_run<KT>(store, hdr[g].off, n);
+        const float *src = zp + start[g];
+        for (uint32_t i = lane; i < n; i += 32) {
+            const float v = src[i];
+            if (i > 0 && !(src[i - 1] <= v)) atomicCAS(status, 0, (int)CDDT_ERR_DEVICE);
+            if (sizeof(KT) == 4) reinterpret_cast<float *>(run)[i] = v;
+            else reinterpret_cast<uint16_t *>(run)[i] = quantise(v, bin_X[g], Q);
+        }
+    }
+}
+
+cddt_status import_store(cddt_s *h, const int64_t *bin_start_host, const float *zp_host, cudaStream_t st)
+{
+    const int64_t nb = h->total_bins;
+    if (bin_start_host[0] != 0) return CDDT_ERR_ARG;
+    std::vector<uint32_t> cnt((size_t)std::max<int64_t>(nb, 1)), start((size_t)std::max<int64_t>(nb, 1));
+    for (int64_t g = 0; g < nb; ++g) {
+        const int64_t a = bin_start_host[g], b = bin_start_host[g + 1];
+        if (b < a || b - a > (int64_t)kMaxBinKeys || b > 0xffffffffll) return CDDT_ERR_ARG;
+        cnt[g] = (uint32_t)(b - a);
+        start[g] = (uint32_t)a;
+    }
+    const int64_t n = bin_start_host[nb];
+    std::vector<float> bin_X;
+    if (h->u16) {
+        std::vector<SliceInfo> tab;
+        slice_tables(h, tab);
+        bin_X.resize((size_t)std::max<int64_t>(nb, 1));
+        for (int s = 0; s < h->S; ++s)
+            for (int b = 0; b < tab[s].nb; ++b) bin_X[tab[s].sbase + b] = tab[s].X;
+    }
+    Buf cnt_d, start_d, zp_d, x_d;
+    CDDT_CUDA(cnt_d.alloc(sizeof(uint32_t) * cnt.size()));
+    CDDT_CUDA(start_d.alloc(sizeof(uint32_t) * start.size()));
+    CDDT_CUDA(zp_d.alloc(sizeof(float) * (size_t)std::max<int64_t>(n, 1)));
+    CDDT_CUDA(cudaMemcpyAsync(cnt_d.p, cnt.data(), sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st));
+    CDDT_CUDA(cudaMemcpyAsync(start_d.p, start.data(), sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st));
+    if (n) CDDT_CUDA(cudaMemcpyAsync(zp_d.p, zp_host, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    if (h->u16) {
+        CDDT_CUDA(x_d.alloc(sizeof(float) * bin_X.size()));
+        CDDT_CUDA(cudaMemcpyAsync(x_d.p, bin_X.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, st));
+    }
+    void *store = nullptr;
+    int64_t nodes = 0;
+    CDDT_TRY(layout_bins(h, cnt_d.as<uint32_t>(), st, &store, &nodes, 0));
+    h->store = store;
+    h->store_nodes = nodes;
+    h->store_cap = std::max<int64_t>(nodes, 1);
+    const unsigned blocks = grid_for(nb * 32, 256);
+    if (h->u16)
+        load_bins_kernel<uint16_t><<<blocks, 256, 0, st>>>(zp_d.as<float>(), start_d.as<uint32_t>(), x_d.as<float>(),
+                                                            h->hdr, h->store, nb, h->Q, h->status);
+    else
+        load_bins_kernel<float><<<blocks, 256, 0, st>>>(zp_d.as<float>(), start_d.as<uint32_t>(), nullptr, h->hdr,
+                                                         h->store, nb, h->Q, h->status);
+    CDDT_CUDA(cudaGetLastError());
+    CDDT_TRY(index_store(h, st));
+    CDDT_CUDA(cudaStreamSynchronize(st));  // the host staging buffers are freed on return
+    return CDDT_OK;
 }
 
 }  // namespace cddt

@@ -25,7 +25,10 @@ cddt_status layout_bins(cddt_s *h, uint32_t *count_dev, cudaStream_t st, void **
                         int64_t *spare_nodes = nullptr);
 cddt_status sort_and_index_any(cddt_s *h, cudaStream_t st);
 cddt_status construct(cddt_s *h, cudaStream_t st);
-cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st);
+// Slice tables, grid and edge map of a new handle, then (build) the store.
+cddt_status init_handle(cddt_s *h, const uint8_t *grid_dev, cudaStream_t st, bool build = true);
+// The store of an initialised handle from an exported CSR (cddt_import).
+cddt_status import_store(cddt_s *h, const int64_t *bin_start_host, const float *zp_host, cudaStream_t st);
 cddt_status prune(cddt_s *h, cudaStream_t st);
 cddt_status update_cells(cddt_s *h, const int32_t *xy, const uint8_t *occ, int32_t n,
                          cudaStream_t st);

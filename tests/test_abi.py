@@ -63,3 +63,11 @@ def test_host_side_argument_errors(lib):
     assert lib.cddt_set_search(None, 0) == ARG
     assert lib.cddt_plan_create(None, 0, None, C.byref(h)) == ARG
     assert lib.cddt_plan_destroy(None) == cddt.CDDT_OK
+    bs = (C.c_int64 * 3)(0, 2, 4)
+    zp = (C.c_float * 4)(0.0, 1.0, 2.0, 3.0)
+    assert lib.cddt_import(fake, 10, 10, 8, 10.0, 0, 0, 2, None, zp, None, C.byref(h)) == ARG
+    assert lib.cddt_import(fake, 10, 10, 8, 10.0, 0, 0, 2, bs, None, None, C.byref(h)) == ARG
+    assert lib.cddt_import(fake, 10, 10, 8, 10.0, 0, 0, -1, bs, zp, None, C.byref(h)) == ARG
+    assert lib.cddt_import(fake, 10, 10, 7, 10.0, 0, 0, 2, bs, zp, None, C.byref(h)) == ARG
+    assert lib.cddt_import(None, 10, 10, 8, 10.0, 0, 0, 2, bs, zp, None, C.byref(h)) == ARG
+    assert lib.cddt_import(fake, 10, 10, 8, 10.0, 0, 0, 2, bs, zp, None, None) == ARG

@@ -215,3 +215,50 @@ def test_update_empty_batch(G):
     d.update_cells(torch.empty((0, 2), dtype=torch.int32, device="cuda"),
                    torch.empty(0, dtype=torch.uint8, device="cuda"))
     assert d.status() == G.CDDT_OK
+
+
+# ------------------------------------------------------------------ import
+
+@pytest.mark.parametrize("u16", [False, True])
+def test_import_round_trip(G, oracle, u16):
+    """cddt_import of an exported store answers exactly as the original,
+    before and after the same update, and restores a pruned store."""
+    g = synth.corridor_map(300, 260, seed=61, r_min=48)
+    N, mr = 72, 400.0
+    d = G.CDDT(dev(g), N, mr, u16=u16)
+    sb, bs, zp = d.export()
+    d2 = G.CDDT.from_export(dev(g), N, mr, bs, zp, u16=u16)
+    sb2, bs2, zp2 = d2.export()
+    assert np.array_equal(bs, bs2) and np.array_equal(zp.view(np.uint32), zp2.view(np.uint32))
+    assert d2.stats()["n_zero_points"] == d.stats()["n_zero_points"]
+    q = gc.random_queries(300, 260, 20000, 62)
+    assert bits_equal(d2.calc_range_many(dev(q)).cpu().numpy(), d.calc_range_many(dev(q)).cpu().numpy())
+    xy, occ = synth.cell_toggles(g, 300, 300, seed=63)
+    d.update_cells(dev(xy), dev(occ))
+    d2.update_cells(dev(xy), dev(occ))
+    assert d2.status() == G.CDDT_OK
+    same = d.export()
+    assert np.array_equal(same[1], d2.export()[1])
+    assert bits_equal(d2.calc_range_many(dev(q)).cpu().numpy(), d.calc_range_many(dev(q)).cpu().numpy())
+    # a pruned store comes back pruned (updates refused)
+    d.prune()
+    _, bsp, zpp = d.export()
+    d3 = G.CDDT.from_export(dev(synth.apply_writes(g, xy, occ)), N, mr, bsp, zpp, u16=u16, pruned=True)
+    assert d3.stats()["pruned"] == 1
+    assert bits_equal(d3.calc_range_many(dev(q)).cpu().numpy(), d.calc_range_many(dev(q)).cpu().numpy())
+    with pytest.raises(G.CDDTError):
+        d3.update_cells(dev(xy[:1]), dev(occ[:1]))
+
+
+def test_import_rejects_mismatched_csr(G):
+    g = synth.rect_map(128, 96, seed=64)
+    d = G.CDDT(dev(g), 40, 200.0)
+    _, bs, zp = d.export()
+    with pytest.raises(G.CDDTError):  # other theta_disc: another bin count
+        G.CDDT.from_export(dev(g), 44, 200.0, bs, zp)
+    bad = zp.copy()
+    i = int(np.argmax(np.diff(bs) > 2))
+    a = bs[i]
+    bad[a], bad[a + 1] = bad[a + 1] + 1.0, bad[a]  # an unsorted bin
+    with pytest.raises(G.CDDTError):
+        G.CDDT.from_export(dev(g), 40, 200.0, bs, bad)
