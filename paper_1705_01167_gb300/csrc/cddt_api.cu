@@ -10,6 +10,7 @@
 
 #include "cddt_internal.cuh"
 #include "cddt_kernels.cuh"
+#include "cddt_trace.cuh"
 
 namespace {
 
@@ -81,12 +82,14 @@ const char *cddt_status_string(cddt_status s)
 cddt_status cddt_build(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t theta_disc, float max_range,
                        uint32_t flags, void *stream, cddt_t *out)
 {
+    CDDT_RANGE("cddt_build");
     if (!out) return CDDT_ERR_ARG;
     *out = nullptr;
     if (!grid_dev || W < 1 || H < 1 || W > 32767 || H > 32767) return CDDT_ERR_ARG;
     if (theta_disc < 2 || (theta_disc & 1) || theta_disc > 65536) return CDDT_ERR_ARG;
     if (!(max_range > 0) || !std::isfinite(max_range)) return CDDT_ERR_ARG;
     if (flags & ~CDDT_ZP_U16) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_build");
     if (!device_ok()) return CDDT_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     cddt_s *h = new cddt_s();
@@ -123,6 +126,7 @@ cddt_status cddt_import(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t t
                         uint32_t flags, int32_t pruned, int64_t total_bins, const int64_t *bin_start_host,
                         const float *zp_host, void *stream, cddt_t *out)
 {
+    CDDT_RANGE("cddt_import");
     if (!out) return CDDT_ERR_ARG;
     *out = nullptr;
     if (!grid_dev || W < 1 || H < 1 || W > 32767 || H > 32767) return CDDT_ERR_ARG;
@@ -131,6 +135,7 @@ cddt_status cddt_import(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t t
     if (flags & ~CDDT_ZP_U16) return CDDT_ERR_ARG;
     if (total_bins < 0 || !bin_start_host) return CDDT_ERR_ARG;
     if (bin_start_host[total_bins] > 0 && !zp_host) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_import");
     if (!device_ok()) return CDDT_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     cddt_s *h = new cddt_s();
@@ -174,18 +179,22 @@ cddt_status cddt_destroy(cddt_t h)
 
 cddt_status cddt_prune(cddt_t h, void *stream)
 {
+    CDDT_RANGE("cddt_prune");
     cddt_status rc = check_handle(h);
     if (rc != CDDT_OK) return rc;
     if (h->pruned) return CDDT_ERR_PRUNED;
+    CDDT_FAULT_POINT("cddt_prune");
     return cddt::prune(h, (cudaStream_t)stream);
 }
 
 cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const uint8_t *occ_dev, int32_t n, void *stream)
 {
+    CDDT_RANGE("cddt_update_cells");
     cddt_status rc = check_handle(h);
     if (rc != CDDT_OK) return rc;
     if (n < 0 || (n > 0 && (!xy_dev || !occ_dev))) return CDDT_ERR_ARG;
     if (h->pruned) return CDDT_ERR_PRUNED;
+    CDDT_FAULT_POINT("cddt_update_cells");
     if (n == 0) return CDDT_OK;
     return cddt::update_cells(h, xy_dev, occ_dev, n, (cudaStream_t)stream);
 }
@@ -193,9 +202,11 @@ cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const uint8_t *oc
 cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_dev, int64_t n, int32_t sort_by_slice,
                                  void *stream)
 {
+    CDDT_RANGE("cddt_calc_range_many");
     cddt_status rc = check_handle(h);
     if (rc != CDDT_OK) return rc;
     if (n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_calc_range_many");
     return cddt::calc_range(h, pose_dev, range_dev, n, sort_by_slice, (cudaStream_t)stream);
 }
 
@@ -203,9 +214,11 @@ cddt_status cddt_sensor_weights(cddt_t h, const float *particles_dev, int64_t P,
                                 const float *obs_dev, int32_t B, int32_t pair_offset, const cddt_beam_model *m,
                                 float *logw_dev, float *ranges_dev, void *stream)
 {
+    CDDT_RANGE("cddt_sensor_weights");
     cddt_status rc = sensor_common(h, particles_dev, P, beam_off_dev, obs_dev, B, pair_offset, m);
     if (rc != CDDT_OK) return rc;
     if (P > 0 && !logw_dev) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_sensor_weights");
     if (P == 0) return CDDT_OK;
     cddt::SensorArgs a{};
     a.part = particles_dev;
@@ -225,9 +238,11 @@ cddt_status cddt_sensor_weights_backward(cddt_t h, const float *particles_dev, i
                                          const cddt_beam_model *m, const float *grad_logw_dev, float *grad_xy_dev,
                                          void *stream)
 {
+    CDDT_RANGE("cddt_sensor_weights_backward");
     cddt_status rc = sensor_common(h, particles_dev, P, beam_off_dev, obs_dev, B, pair_offset, m);
     if (rc != CDDT_OK) return rc;
     if (P > 0 && (!grad_logw_dev || !grad_xy_dev)) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_sensor_weights_backward");
     if (P == 0) return CDDT_OK;
     cddt::SensorArgs a{};
     a.part = particles_dev;
@@ -246,9 +261,11 @@ cddt_status cddt_sensor_weights_fwd_bwd(cddt_t h, const float *particles_dev, in
                                         const float *obs_dev, int32_t B, int32_t pair_offset,
                                         const cddt_beam_model *m, float *logw_dev, float *grad_xy_dev, void *stream)
 {
+    CDDT_RANGE("cddt_sensor_weights_fwd_bwd");
     cddt_status rc = sensor_common(h, particles_dev, P, beam_off_dev, obs_dev, B, pair_offset, m);
     if (rc != CDDT_OK) return rc;
     if (P > 0 && (!logw_dev || !grad_xy_dev)) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_sensor_weights_fwd_bwd");
     if (P == 0) return CDDT_OK;
     cddt::SensorArgs a{};
     a.part = particles_dev;

@@ -71,3 +71,22 @@ def test_host_side_argument_errors(lib):
     assert lib.cddt_import(fake, 10, 10, 7, 10.0, 0, 0, 2, bs, zp, None, C.byref(h)) == ARG
     assert lib.cddt_import(None, 10, 10, 8, 10.0, 0, 0, 2, bs, zp, None, C.byref(h)) == ARG
     assert lib.cddt_import(fake, 10, 10, 8, 10.0, 0, 0, 2, bs, zp, None, None) == ARG
+
+
+def test_host_fault_injection(lib, monkeypatch):
+    """CDDT_FAULT makes an entry point return a failure status after its
+    argument checks and before any device call (the only calls made here
+    return at the fault point)."""
+    from paper_1705_01167_gb300 import cddt
+    h = C.c_void_p(0x1234)
+    fake = C.c_void_p(0x1000)
+    for kind, status in (("oom", cddt.CDDT_ERR_OOM), ("launch", cddt.CDDT_ERR_CUDA),
+                         ("timeout", cddt.CDDT_ERR_TIMEOUT)):
+        monkeypatch.setenv("CDDT_FAULT", kind)
+        assert lib.cddt_build(fake, 10, 10, 8, 10.0, 0, None, C.byref(h)) == status
+        assert not h.value  # no handle made
+        monkeypatch.setenv("CDDT_FAULT", f"{kind}:cddt_build")
+        assert lib.cddt_build(fake, 10, 10, 8, 10.0, 0, None, C.byref(h)) == status
+    # argument errors still come first
+    monkeypatch.setenv("CDDT_FAULT", "oom")
+    assert lib.cddt_build(fake, 0, 10, 8, 10.0, 0, None, C.byref(h)) == cddt.CDDT_ERR_ARG

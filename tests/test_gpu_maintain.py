@@ -262,3 +262,40 @@ def test_import_rejects_mismatched_csr(G):
     bad[a], bad[a + 1] = bad[a + 1] + 1.0, bad[a]  # an unsorted bin
     with pytest.raises(G.CDDTError):
         G.CDDT.from_export(dev(g), 40, 200.0, bs, bad)
+
+
+def test_injected_faults_leave_handles_usable(G, oracle, monkeypatch):
+    """Host-injected failures (CDDT_FAULT) surface as errors of the named
+    call; the handle and plan keep working once the variable is cleared."""
+    g = synth.rect_map(96, 80, seed=71)
+    d = G.CDDT(dev(g), 36, 150.0)
+    o = oracle.OracleCDDT(g, 36, 150.0)
+    q = dev(gc.random_queries(96, 80, 5000, 72))
+    before = d.export()
+    monkeypatch.setenv("CDDT_FAULT", "launch:cddt_calc_range_many")
+    with pytest.raises(G.CDDTError) as e:
+        d.calc_range_many(q)
+    assert e.value.status == G.CDDT_ERR_CUDA
+    monkeypatch.setenv("CDDT_FAULT", "oom:cddt_update_cells")
+    xy, occ = synth.cell_toggles(g, 50, 50, seed=73)
+    with pytest.raises(G.CDDTError) as e:
+        d.update_cells(dev(xy), dev(occ))
+    assert e.value.status == G.CDDT_ERR_OOM
+    after = d.export()
+    assert np.array_equal(before[1], after[1]) and np.array_equal(before[2], after[2])
+    bo = dev(synth.beam_offsets(61))
+    obs = dev(gc.observations(o, synth.uniform_particles(g, 1, seed=74)[0], synth.beam_offsets(61), 150.0))
+    parts = dev(synth.uniform_particles(g, 300, seed=75))
+    logw = torch.empty(300, device="cuda")
+    plan = G.Plan([dict(map=d, particles=parts, beam_off=bo, obs=obs, model=G.beam_model(150.0), logw=logw,
+                        pair_offset=synth.pair_offset(61))])
+    monkeypatch.setenv("CDDT_FAULT", "timeout:cddt_plan_run")
+    with pytest.raises(G.CDDTError) as e:
+        plan.run()
+    assert e.value.status == G.CDDT_ERR_TIMEOUT
+    monkeypatch.delenv("CDDT_FAULT")
+    plan.run()
+    want = d.sensor_weights(parts, bo, obs, G.beam_model(150.0), synth.pair_offset(61))
+    assert torch.allclose(logw, want, rtol=1e-5, atol=1e-5)
+    assert bits_equal(d.calc_range_many(q).cpu().numpy(), o.calc_range(q.cpu().numpy()))
+    plan.close()
