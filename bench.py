@@ -361,13 +361,22 @@ def bench_corridor(args, G, torch, dev, world, rank):
     obs_h = torch.from_numpy(obs).pin_memory()
     logw_h = torch.empty(S * P, dtype=torch.float32).pin_memory()
 
-    def e2e():
+    def e2e_copy():
         parts_d.copy_(parts_h, non_blocking=True)
         obs_d.copy_(obs_h, non_blocking=True)
         plan.run()
         logw_h.copy_(logw_d, non_blocking=True)
-    ms_e = timed(e2e, k2, 2)
+    ms_c = timed(e2e_copy, k2, 2)
+    copy_ms = max_over_ranks(world, statistics.mean(ms_c))
+    # the same step on a plan whose particles, scans and log-weights are the
+    # page-locked host buffers: the kernel reads the inputs and writes the
+    # results across the host link itself (no copy-engine transfers)
+    plan_h = G.Plan([dict(map=d, particles=parts_h[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_h[t], model=m,
+                          logw=logw_h[t * P:(t + 1) * P], pair_offset=D) for t in range(S)])
+    plan_h.set_shape(**shape)
+    ms_e = timed(plan_h.run, k2, 2)
     e2e_ms = max_over_ranks(world, statistics.mean(ms_e))
+    plan_h.close()
 
     line = base_line(args, world, value, ms_step, "corridor2000",
                      {"launch": f"persistent batched, autotuned {shape}", "zero_points": st0["n_zero_points"],
@@ -378,7 +387,9 @@ def bench_corridor(args, G, torch, dev, world, rank):
                      "kernel": "batched_kernel", "algorithmic_bytes_per_launch": alg, "work": work},
         "e2e": {"value": world * rays_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(parts_h.numel() * 4 + obs_h.numel() * 4),
-                "d2h_bytes_per_step": int(logw_h.numel() * 4)},
+                "d2h_bytes_per_step": int(logw_h.numel() * 4),
+                "path": "plan on page-locked host buffers (kernel reads and writes them across the host link)",
+                "copy_engine_value": world * rays_per_step / (copy_ms * 1e-3)},
         "gpu_launches": args.steps, "clocks": clocks,
         "build_ms": st0["build_ms"], "build_wall_s": build_wall, **extra})
     if not args.no_cpu and rank == 0:

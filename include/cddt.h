@@ -204,8 +204,12 @@ CDDT_API cddt_status cddt_sensor_weights_fwd_bwd(cddt_t h, const float *particle
 
 /* One filter of a batch: its CDDT, particles, scan and model.  Several
  * filters may share a handle (for example successive filter steps on one
- * map).  All pointers are device memory owned by the caller and must stay
- * valid while the plan is used. */
+ * map).  All pointers are owned by the caller and must stay valid while the
+ * plan is used.  They are device memory, or page-locked host memory
+ * (cudaHostAlloc / cudaMallocHost, which kernels address directly under
+ * unified addressing): the plan's kernel then reads the particles and writes
+ * the log-weights across the host link itself, with no separate copy; the
+ * host may read logw once `stream` has passed the run. */
 typedef struct {
     cddt_t map;
     const float *particles_dev; /* [P][3] */

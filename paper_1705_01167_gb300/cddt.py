@@ -141,6 +141,18 @@ def _stream(stream=None) -> int:
     return s.cuda_stream
 
 
+def _dev_or_pinned(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    """A CUDA tensor, or a page-locked host tensor (kernels address it
+    directly under unified addressing)."""
+    if isinstance(t, torch.Tensor) and not t.is_cuda and (t.is_pinned() or t.numel() == 0):
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+    return _dev(t, dtype, name)
+
+
 def _dev(t: torch.Tensor, dtype, name: str, shape=None) -> torch.Tensor:
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
@@ -320,10 +332,11 @@ class CDDT:
                    "cddt_calc_range_many_noalloc")
         return out
 
-    def _sensor_args(self, particles, beam_off, obs):
-        _dev(particles, torch.float32, "particles")
-        _dev(beam_off, torch.float32, "beam_off")
-        _dev(obs, torch.float32, "obs")
+    def _sensor_args(self, particles, beam_off, obs, pinned_ok: bool = False):
+        check = _dev_or_pinned if pinned_ok else _dev
+        check(particles, torch.float32, "particles")
+        check(beam_off, torch.float32, "beam_off")
+        check(obs, torch.float32, "obs")
         P = particles.numel() // 3
         B = beam_off.numel()
         if particles.numel() != 3 * P or obs.numel() != B:
@@ -410,7 +423,9 @@ class SensorWeights(torch.autograd.Function):
 
 class Plan:
     """Many filters (maps of any size, any particle count) weighted in one
-    persistent launch (``cddt_plan_*``), optionally replayed as a CUDA graph."""
+    persistent launch (``cddt_plan_*``), optionally replayed as a CUDA graph.
+    Particles, scans and log-weights may be CUDA tensors or page-locked host
+    tensors (read and written by the kernel across the host link)."""
 
     def __init__(self, filters: list[dict], stream=None):
         L = load()
@@ -418,8 +433,8 @@ class Plan:
         self._keep = []
         for i, f in enumerate(filters):
             m: CDDT = f["map"]
-            P, B = m._sensor_args(f["particles"], f["beam_off"], f["obs"])
-            _dev(f["logw"], torch.float32, "logw")
+            P, B = m._sensor_args(f["particles"], f["beam_off"], f["obs"], pinned_ok=True)
+            _dev_or_pinned(f["logw"], torch.float32, "logw")
             arr[i] = Filter(m.handle.value, f["particles"].data_ptr(), P, f["beam_off"].data_ptr(),
                             f["obs"].data_ptr(), B, int(f.get("pair_offset", 0)), f["model"],
                             f["logw"].data_ptr())

@@ -162,3 +162,38 @@ def test_plan_more_filters_than_one_launch(G, oracle):
     plan.launch_graph()
     _check(filters, refs)
     plan.close()
+
+
+def test_plan_on_pinned_host_buffers(G, batch):
+    """A plan may take page-locked host tensors for particles, scans and
+    log-weights: the kernel reads and writes them itself, bit for bit as on
+    device buffers."""
+    maps, filters, refs = batch
+    dev_plan = G.Plan(filters)
+    dev_plan.run()
+    torch.cuda.synchronize()
+    host = []
+    for f in filters:
+        h = dict(f)
+        h["particles"] = f["particles"].cpu().pin_memory()
+        h["obs"] = f["obs"].cpu().pin_memory()
+        h["beam_off"] = f["beam_off"].cpu().pin_memory()
+        h["logw"] = torch.full(f["logw"].shape, float("nan")).pin_memory()
+        host.append(h)
+    plan = G.Plan(host)
+    plan.run()
+    torch.cuda.synchronize()
+    for f, h in zip(filters, host):
+        assert torch.equal(h["logw"], f["logw"].cpu())
+    for h in host:
+        h["logw"].fill_(float("nan"))
+    plan.launch_graph()
+    torch.cuda.synchronize()
+    for f, h in zip(filters, host):
+        assert torch.equal(h["logw"], f["logw"].cpu())
+    with pytest.raises(ValueError):  # pageable host memory is refused
+        bad = dict(filters[0])
+        bad["logw"] = torch.empty(filters[0]["logw"].shape)
+        G.Plan([bad])
+    plan.close()
+    dev_plan.close()
