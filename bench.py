@@ -167,6 +167,36 @@ def algorithmic_bytes(work: dict, P: int) -> int:
     return 8 * work["traversals"] + 4 * work["probes"] + 4 * work["paired"] + 17 * P
 
 
+def sector_bytes(work: dict, P: int) -> int:
+    """Sector bytes of one sensor launch: 32 B per sector a sorted-CSR binary
+    search touches (the bin's offsets, the probes while the range spans more
+    than one sector, the last sector) plus 17 B per particle."""
+    return 32 * work["sectors"] + 17 * P
+
+
+def gather_bandwidth(G, torch, dev):
+    """Random 32-byte sector gather bandwidth (GB/s) of HBM (a 4 GiB buffer,
+    well beyond L2) and of L2 (a 32 MiB buffer), timed with CUDA events."""
+    out = {}
+    for name, nbytes, reads in (("hbm", 4 << 30, 1 << 27), ("l2", 32 << 20, 1 << 27)):
+        buf = torch.empty(nbytes // 4, dtype=torch.int32, device=dev).fill_(1)
+        sink = torch.zeros(1, dtype=torch.int64, device=dev)
+        G.gather_probe(buf, reads, 7, sink)
+        torch.cuda.synchronize()
+        ts = []
+        for i in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            G.gather_probe(buf, reads, 11 + i, sink)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name] = reads * 32 / (statistics.median(ts) * 1e-3) / 1e9
+        del buf
+    torch.cuda.empty_cache()
+    return out
+
+
 def add_work(acc: dict, w: dict):
     for k, v in w.items():
         acc[k] = acc.get(k, 0) + v
@@ -317,11 +347,28 @@ def bench_corridor(args, G, torch, dev, world, rank):
     alg = algorithmic_bytes(work, S * P)
     peak, peak_kind = measured_peaks()
     achieved = alg / (ms_step * 1e-3) / 1e9
+    # the sorted-CSR sector count against this GPU's random-sector gather
+    # bandwidth (the store, 288 MB, is larger than L2: the HBM figure)
+    sec = sector_bytes(work, S * P)
+    gbw = gather_bandwidth(G, torch, dev)
 
     extra = {}
     k2 = max(3, args.steps // 2)
     ms_g = timed(plan.launch_graph, k2, 2)
     extra["graph_rays_per_s"] = rays_per_step / (statistics.mean(ms_g) * 1e-3)
+
+    # the uniform-particle variant (global localization: each filter's
+    # particles spread over the whole free space)
+    upart = np.stack([synth.uniform_particles(w["grid"], P, seed=synth.SEED_PARTICLES + 5000 + t
+                                              + 100000 * RK.seed_offset(rank)) for t in range(S)])
+    upart_d = torch.from_numpy(upart.reshape(-1, 3)).to(dev).contiguous()
+    plan_u = G.Plan([dict(map=d, particles=upart_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t], model=m,
+                          logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(S)])
+    shape_u = plan_u.autotune()
+    ms_u = timed(plan_u.run, k2, 2)
+    extra["uniform_particles_rays_per_s"] = rays_per_step / (statistics.mean(ms_u) * 1e-3)
+    extra["uniform_particles_shape"] = shape_u
+    plan_u.close()
 
     def sequential():
         for t in range(S):
@@ -384,7 +431,10 @@ def bench_corridor(args, G, torch, dev, world, rank):
     line.update({
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": recorded_traffic("batched_kernel", S * P), "peak_kind": peak_kind,
-                     "kernel": "batched_kernel", "algorithmic_bytes_per_launch": alg, "work": work},
+                     "kernel": "batched_kernel", "algorithmic_bytes_per_launch": alg, "work": work,
+                     "sector_bytes_per_launch": sec, "sector_gbs": sec / (ms_step * 1e-3) / 1e9,
+                     "gather_gbs_measured": gbw,
+                     "sector_frac_of_hbm_gather": sec / (ms_step * 1e-3) / 1e9 / gbw["hbm"]},
         "e2e": {"value": world * rays_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(parts_h.numel() * 4 + obs_h.numel() * 4),
                 "d2h_bytes_per_step": int(logw_h.numel() * 4),

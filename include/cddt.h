@@ -312,13 +312,28 @@ CDDT_API cddt_status cddt_export_grid(cddt_t h, uint8_t *grid_host, uint8_t *edg
 
 /* Per-launch work figures of a cddt_sensor_weights call with the same
  * arguments, for roofline accounting (no ranges or weights are produced):
- *   out_host int64 [6] = { traversals, beams cast, searches with a
+ *   out_host int64 [7] = { traversals, beams cast, searches with a
  *   non-empty bin, sum over searches of ceil(log2(k_b + 1)) for bin size
- *   k_b, paired reverse beams, particles passing the occupancy check }.
+ *   k_b, paired reverse beams, particles passing the occupancy check, sum
+ *   over searches of the 32-byte sectors a binary search of the bin as a
+ *   sorted CSR touches: 1 for its two offsets, plus (k_b > 0) 1 per probe
+ *   while the remaining range spans more than one sector (8 float32 or 16
+ *   16-bit keys) and 1 for the last sector }.
  * Synchronises `stream`.  Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_sensor_work(cddt_t h, const float *particles_dev, int64_t P,
                              const float *beam_off_dev, int32_t B, int32_t pair_offset,
                              int64_t *out_host, void *stream);
+
+/* Measurement helper, no counterpart in the paper: read `sectors` 32-byte
+ * sectors of the device buffer buf_dev (32-byte aligned; bytes >= 32, a
+ * multiple of 32) at
+ * pseudo-random sector indices (a hash of seed and the read's index), one
+ * 256-bit load each, and XOR them into *sink_dev (device, one uint64) so
+ * that the loads are not dead.  Timed by the caller, it gives the random
+ * sector gather bandwidth of HBM (a buffer larger than L2) or of L2 (a
+ * smaller one).  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_gather_probe(const void *buf_dev, int64_t bytes, int64_t sectors, uint64_t seed,
+                                       uint64_t *sink_dev, void *stream);
 
 /* A short message for a status code (static storage). */
 CDDT_API const char *cddt_status_string(cddt_status s);

@@ -182,6 +182,26 @@ class Params:
         return keep[:a.size].astype(bool)
 
 
+def sorted_search_sectors(kb, keys_per_sector: int = 8):
+    """32-byte sectors a binary search of a sorted CSR bin of kb keys
+    touches (the roofline's sector count): one for the bin's two offsets;
+    for a non-empty bin, one per probe while the remaining range spans more
+    than one sector (ceil(log2(kb / keys_per_sector)) halvings) and one for
+    the last sector.  Array in, array out."""
+    k = np.asarray(kb, np.int64)
+    out = np.ones(k.shape, np.int64)
+    for idx in np.ndindex(k.shape):
+        r = int(k[idx])
+        if r <= 0:
+            continue
+        c = 0
+        while r > keys_per_sector:
+            r = (r + 1) // 2
+            c += 1
+        out[idx] = 2 + c
+    return out
+
+
 class OracleCDDT:
     """O2: the plain CDDT built on the CPU (Section IV-A), with query, prune,
     update, beam-model weights and gradient."""

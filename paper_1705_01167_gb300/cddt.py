@@ -30,7 +30,7 @@ EXPORTED = (
     "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
-    "cddt_import",
+    "cddt_import", "cddt_gather_probe",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
             "cddt_get_status": (st, [vp]),
             "cddt_export": (st, [vp, vp, vp, vp]),
             "cddt_import": (st, [vp, i32, i32, i32, f32, u32, i32, i64, vp, vp, vp, C.POINTER(vp)]),
+            "cddt_gather_probe": (st, [vp, i64, i64, C.c_uint64, vp, vp]),
             "cddt_export_grid": (st, [vp, vp, vp]),
             "cddt_sensor_work": (st, [vp, vp, i64, vp, i32, i32, vp, vp]),
             "cddt_status_string": (C.c_char_p, [st]),
@@ -389,13 +390,13 @@ class CDDT:
         import numpy as np
         _dev(particles, torch.float32, "particles")
         _dev(beam_off, torch.float32, "beam_off")
-        out = np.zeros(6, np.int64)
+        out = np.zeros(7, np.int64)
         with torch.cuda.device(self.device):
             _check(load().cddt_sensor_work(self._h, _ptr(particles), particles.numel() // 3,
                                            _ptr(beam_off), beam_off.numel(), pair_offset,
                                            out.ctypes.data_as(C.c_void_p), _stream(stream)),
                    "cddt_sensor_work")
-        keys = ("traversals", "beams", "nonempty", "probes", "paired", "passed")
+        keys = ("traversals", "beams", "nonempty", "probes", "paired", "passed", "sectors")
         return dict(zip(keys, (int(v) for v in out)))
 
 
@@ -419,6 +420,19 @@ class SensorWeights(torch.autograd.Function):
         grad = torch.zeros_like(p)
         grad[:, :2] = g
         return grad, None, None, None, None, None
+
+
+def gather_probe(buf: torch.Tensor, sectors: int, seed: int = 1, sink: torch.Tensor | None = None, stream=None):
+    """``cddt_gather_probe``: read ``sectors`` random 32-byte sectors of the
+    CUDA buffer ``buf`` (time it with CUDA events)."""
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("buf must be a contiguous CUDA tensor")
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.int64, device=buf.device)
+    with torch.cuda.device(buf.device):
+        _check(load().cddt_gather_probe(_ptr(buf), buf.numel() * buf.element_size() // 32 * 32, int(sectors),
+                                        int(seed), _ptr(sink), _stream(stream)), "cddt_gather_probe")
+    return sink
 
 
 class Plan:

@@ -288,12 +288,12 @@ cddt_status cddt_sensor_work(cddt_t h, const float *particles_dev, int64_t P, co
     cddt_status rc = sensor_common(h, particles_dev, P, beam_off_dev, beam_off_dev, B, pair_offset, &dummy);
     if (rc != CDDT_OK) return rc;
     if (!out_host) return CDDT_ERR_ARG;
-    std::memset(out_host, 0, sizeof(int64_t) * 6);
+    std::memset(out_host, 0, sizeof(int64_t) * 7);
     if (P == 0) return CDDT_OK;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *w = nullptr;
-    CDDT_CUDA(cudaMalloc(&w, sizeof(unsigned long long) * 6));
-    cudaMemsetAsync(w, 0, sizeof(unsigned long long) * 6, st);
+    CDDT_CUDA(cudaMalloc(&w, sizeof(unsigned long long) * 7));
+    cudaMemsetAsync(w, 0, sizeof(unsigned long long) * 7, st);
     cddt::SensorArgs a{};
     a.part = particles_dev;
     a.P = P;
@@ -304,14 +304,14 @@ cddt_status cddt_sensor_work(cddt_t h, const float *particles_dev, int64_t P, co
     a.bc = cddt::make_beam_consts(dummy);
     a.work = w;
     rc = cddt::launch_sensor(h, a, 3, st);
-    unsigned long long host[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long host[7] = {0, 0, 0, 0, 0, 0, 0};
     if (rc == CDDT_OK) {
         cudaError_t e = cudaMemcpyAsync(host, w, sizeof(host), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cddt::cuda_status(e);
     }
     cudaFree(w);
-    for (int q = 0; q < 6; ++q) out_host[q] = (int64_t)host[q];
+    for (int q = 0; q < 7; ++q) out_host[q] = (int64_t)host[q];
     return rc;
 }
 

@@ -14,13 +14,27 @@ enum { MODE_FWD = 0, MODE_BWD = 1, MODE_FWDBWD = 2, MODE_WORK = 3 };
 
 // Work figures of one particle's traversal slot (MODE_WORK).
 struct WorkAcc {
-    unsigned long long trav = 0, beams = 0, nonempty = 0, probes = 0, paired = 0;
+    unsigned long long trav = 0, beams = 0, nonempty = 0, probes = 0, paired = 0, sectors = 0;
 };
 
 __device__ __forceinline__ int ceil_log2p1(int kb)
 {
     // ceil(log2(kb + 1)) for kb >= 0
     return kb <= 0 ? 0 : 32 - __clz((unsigned)kb);
+}
+
+// 32-byte sectors a binary search of a sorted CSR bin of kb keys touches
+// (kps keys per sector): one for the bin's two offsets, one per probe while
+// the remaining range spans more than a sector, one for the last sector.
+__device__ __forceinline__ int sorted_sectors(int kb, int kps)
+{
+    if (kb <= 0) return 1;
+    int r = kb, c = 0;
+    while (r > kps) {
+        r = (r + 1) >> 1;
+        ++c;
+    }
+    return 2 + c;
 }
 
 // One particle's beams in traversal slots t = lane, lane + TPP, ... ; smem
@@ -86,6 +100,7 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const BeamConst
                 w.trav++;
                 w.nonempty += ci.kb > 0;
                 w.probes += ceil_log2p1(ci.kb);
+                w.sectors += sorted_sectors(ci.kb, 32 / (int)sizeof(KT));
             }
             if (j >= 0 && cj.kb >= 0) {
                 w.beams++;
@@ -94,6 +109,7 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const BeamConst
                     w.trav++;
                     w.nonempty += cj.kb > 0;
                     w.probes += ceil_log2p1(cj.kb);
+                    w.sectors += sorted_sectors(cj.kb, 32 / (int)sizeof(KT));
                 }
             }
             continue;
@@ -188,9 +204,9 @@ __global__ void __launch_bounds__(256, 6) sensor_kernel(MapView m, SensorArgs a)
         if (lane == 0 && valid) write_particle(a, MODE, p, acc, gx, gy);
     }
     if (MODE == MODE_WORK) {
-        unsigned long long v[6] = {w.trav, w.beams, w.nonempty, w.probes, w.paired, passed};
+        unsigned long long v[7] = {w.trav, w.beams, w.nonempty, w.probes, w.paired, passed, w.sectors};
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
+        for (int q = 0; q < 7; ++q) {
             unsigned long long s = v[q];
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if ((threadIdx.x & 31) == 0 && s) atomicAdd(a.work + q, s);

@@ -279,6 +279,7 @@ def test_work_counts_match_oracle(G, oracle):
     assert w["traversals"] == int(trav.sum())
     assert w["nonempty"] == int((trav & (kb > 0)).sum())
     assert w["probes"] == int(lg[trav].sum())
+    assert w["sectors"] == int(oracle.sorted_search_sectors(kb[trav], 8).sum())
     gx = np.floor(parts[:, 0] + np.float32(0.5))
     gy = np.floor(parts[:, 1] + np.float32(0.5))
     inmap = (gx >= 0) & (gx < 256) & (gy >= 0) & (gy < 256)

@@ -615,3 +615,13 @@ def test_gradient_matches_finite_differences(oracle):
             assert np.linalg.norm(fd - g0) <= 1e-3 * scale + 1e-9, (t, i, fd, g0)
             n_beam += 1
     assert n_part > 100 and nonzero > 50 and n_beam > 500
+
+
+def test_sorted_search_sectors_pins():
+    """The sector count of a sorted-CSR binary search on hand-checked sizes:
+    an empty bin touches only its offsets; up to 8 keys fit one sector; 9 to
+    16 keys take one halving, 17 to 32 two."""
+    from oracle import oracle as O
+    got = O.sorted_search_sectors([0, 1, 8, 9, 16, 17, 32, 33, 1000], 8)
+    assert list(got) == [1, 2, 2, 3, 3, 4, 4, 5, 9]
+    assert list(O.sorted_search_sectors([16, 17], 16)) == [2, 3]
