@@ -389,6 +389,23 @@ def bench_corridor(args, G, torch, dev, world, rank):
     ms_o = timed(lambda: d.calc_range_many(sw, sort_by_slice=True, out=out), 5, 2)
     extra["sweep_rays_per_s"] = sw.shape[0] / (statistics.mean(ms_u) * 1e-3)
     extra["sweep_sorted_rays_per_s"] = sw.shape[0] / (statistics.mean(ms_o) * 1e-3)
+    # the "grid" benchmark of Section V: every 4th cell centre in x and y and
+    # 200 headings (50 M states, x fastest)
+    gq = torch.from_numpy(WL.grid_states(grid.shape[1], grid.shape[0], 4, 200)).to(dev)
+    gout = torch.empty(gq.shape[0], dtype=torch.float32, device=dev)
+    ms_grid = timed(lambda: d.calc_range_many(gq, out=gout), 5, 2)
+    extra["grid_sweep_rays_per_s"] = gq.shape[0] / (statistics.mean(ms_grid) * 1e-3)
+    # per-warp latency (32 consecutive queries, one per lane) of 1 M random and
+    # 1 M grid states, the GPU counterpart of the paper's per-query violins
+    lat = {}
+    for name, qs in (("random", sw[:1 << 20]), ("grid", gq[:1 << 20])):
+        d.calc_range_timed(qs)
+        _, cyc = d.calc_range_timed(qs)
+        c = cyc.double().cpu().numpy()
+        lat[name] = {"p25": float(np.percentile(c, 25)), "median": float(np.median(c)),
+                     "p75": float(np.percentile(c, 75)), "p99": float(np.percentile(c, 99)), "mean": float(c.mean())}
+    extra["warp_latency_cycles"] = lat
+    del gq, gout
 
     dp = G.CDDT(grid, w["theta_disc"], mr)
     dp.prune()

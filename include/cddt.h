@@ -138,6 +138,15 @@ CDDT_API cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const ui
 CDDT_API cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
                                  int32_t sort_by_slice, void *stream);
 
+/* Ray casting as cddt_calc_range_many (unsorted), one query per thread,
+ * with the latency of every warp of 32 consecutive queries: warp_cycles_dev
+ * int64 [ceil(n / 32)] receives the SM clock cycles between the warp reading
+ * its poses and its last range being written.  The GPU counterpart of the
+ * paper's per-query completion times (its latency violins, Section V):
+ * cycles per warp of queries, not per query.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_calc_range_timed(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
+                                           int64_t *warp_cycles_dev, void *stream);
+
 /* Slice-sorted ray casting that allocates no device memory.  The paper has
  * no counterpart: this entry point serves callers that cannot call
  * cudaMalloc while they run -- an application that reserves all device

@@ -30,7 +30,7 @@ EXPORTED = (
     "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
-    "cddt_import", "cddt_gather_probe",
+    "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
             "cddt_export": (st, [vp, vp, vp, vp]),
             "cddt_import": (st, [vp, i32, i32, i32, f32, u32, i32, i64, vp, vp, vp, C.POINTER(vp)]),
             "cddt_gather_probe": (st, [vp, i64, i64, C.c_uint64, vp, vp]),
+            "cddt_calc_range_timed": (st, [vp, vp, vp, i64, vp, vp]),
             "cddt_export_grid": (st, [vp, vp, vp]),
             "cddt_sensor_work": (st, [vp, vp, i64, vp, i32, i32, vp, vp]),
             "cddt_status_string": (C.c_char_p, [st]),
@@ -343,6 +344,18 @@ class CDDT:
         if particles.numel() != 3 * P or obs.numel() != B:
             raise ValueError("particles must be [P, 3] and obs [B] like beam_off")
         return P, B
+
+    def calc_range_timed(self, poses: torch.Tensor, stream=None):
+        """``cddt_calc_range_timed``: (ranges [n], SM cycles of each warp of 32
+        consecutive queries [ceil(n / 32)])."""
+        _dev(poses, torch.float32, "poses")
+        n = poses.numel() // 3
+        out = torch.empty(n, dtype=torch.float32, device=poses.device)
+        cyc = torch.empty((n + 31) // 32, dtype=torch.int64, device=poses.device)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_calc_range_timed(self._h, _ptr(poses), _ptr(out), n, _ptr(cyc), _stream(stream)),
+                   "cddt_calc_range_timed")
+        return out, cyc
 
     def sensor_weights(self, particles, beam_off, obs, model: BeamModel, pair_offset: int = 0,
                        want_ranges: bool = False, logw=None, stream=None):

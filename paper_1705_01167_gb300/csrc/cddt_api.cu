@@ -210,6 +210,18 @@ cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_d
     return cddt::calc_range(h, pose_dev, range_dev, n, sort_by_slice, (cudaStream_t)stream);
 }
 
+cddt_status cddt_calc_range_timed(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
+                                  int64_t *warp_cycles_dev, void *stream)
+{
+    CDDT_RANGE("cddt_calc_range_timed");
+    cddt_status rc = check_handle(h);
+    if (rc != CDDT_OK) return rc;
+    if (n < 0 || (n > 0 && (!pose_dev || !range_dev || !warp_cycles_dev))) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_calc_range_timed");
+    return cddt::calc_range_timed(h, pose_dev, range_dev, n, reinterpret_cast<long long *>(warp_cycles_dev),
+                                  (cudaStream_t)stream);
+}
+
 cddt_status cddt_sensor_weights(cddt_t h, const float *particles_dev, int64_t P, const float *beam_off_dev,
                                 const float *obs_dev, int32_t B, int32_t pair_offset, const cddt_beam_model *m,
                                 float *logw_dev, float *ranges_dev, void *stream)

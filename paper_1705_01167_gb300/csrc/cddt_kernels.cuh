@@ -49,6 +49,8 @@ struct SensorArgs {
 };
 cddt_status launch_sensor(const cddt_s *h, const SensorArgs &a, int mode, cudaStream_t st);
 cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int sorted, cudaStream_t st);
+cddt_status calc_range_timed(cddt_s *h, const float *pose, float *out, int64_t n, long long *cycles,
+                             cudaStream_t st);
 // The slice-sorted cast on caller-provided scratch of sorted_scratch_bytes(h, n)
 // bytes (cddt_query.cu); returns CDDT_ERR_ARG when the scratch is too small.
 int64_t sorted_scratch_bytes(const cddt_s *h, int64_t n);

@@ -49,6 +49,41 @@ __global__ void calc_range_kernel(MapView m, const float *pose, float *out, int6
     }
 }
 
+// One query per thread; lane 0 of each warp records the SM cycles from the
+// warp's pose loads to its last range store.
+template <typename KT, int SEARCH>
+__global__ void calc_range_timed_kernel(MapView m, const float *pose, float *out, int64_t n, long long *cycles)
+{
+    const uint64_t pol = policy_evict_last();
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __syncwarp();
+    const long long t0 = clock64();
+    if (q < n) {
+        const float x = __ldg(pose + 3 * q), y = __ldg(pose + 3 * q + 1), th = __ldg(pose + 3 * q + 2);
+        out[q] = cast_one<KT, SEARCH>(m, x, y, th, pol).r;
+    }
+    __syncwarp();
+    const long long t1 = clock64();
+    if ((threadIdx.x & 31) == 0 && q < n) cycles[q >> 5] = t1 - t0;
+}
+
+cddt_status calc_range_timed(cddt_s *h, const float *pose, float *out, int64_t n, long long *cycles,
+                             cudaStream_t st)
+{
+    if (n == 0) return CDDT_OK;
+    MapView m = h->view();
+    const int threads = 256;
+    const int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 0x7fffffff) return CDDT_ERR_ARG;
+    const bool bin = h->search == CDDT_SEARCH_BINARY;
+    if (h->u16 && bin) calc_range_timed_kernel<uint16_t, CDDT_SEARCH_BINARY><<<(unsigned)blocks, threads, 0, st>>>(m, pose, out, n, cycles);
+    else if (h->u16) calc_range_timed_kernel<uint16_t, CDDT_SEARCH_TREE><<<(unsigned)blocks, threads, 0, st>>>(m, pose, out, n, cycles);
+    else if (bin) calc_range_timed_kernel<float, CDDT_SEARCH_BINARY><<<(unsigned)blocks, threads, 0, st>>>(m, pose, out, n, cycles);
+    else calc_range_timed_kernel<float, CDDT_SEARCH_TREE><<<(unsigned)blocks, threads, 0, st>>>(m, pose, out, n, cycles);
+    CDDT_CUDA(cudaGetLastError());
+    return CDDT_OK;
+}
+
 // Slice bucket of a query: its stored slice, or S when no search is needed.
 __device__ __forceinline__ int slice_bucket(const MapView &m, float x, float y, float th)
 {

@@ -39,6 +39,17 @@ def gt_queries(gt: np.ndarray, beam_off: np.ndarray) -> np.ndarray:
                                      (np.float32(p[2]) + beam_off)], 1) for p in gt]).astype(np.float32)
 
 
+def grid_states(W: int, H: int, stride: int, n_theta: int) -> np.ndarray:
+    """The "grid" benchmark's states (Section V): a uniformly spaced grid over
+    (x, y, theta), every stride-th cell centre in x and y and n_theta headings
+    2 pi k / n_theta; x varies fastest, then y, then theta.  float32 [n, 3]."""
+    xs = np.arange(0, W, stride, dtype=np.float64)
+    ys = np.arange(0, H, stride, dtype=np.float64)
+    ts = 2.0 * np.pi * np.arange(n_theta, dtype=np.float64) / n_theta
+    t, y, x = np.meshgrid(ts, ys, xs, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), t.ravel()], axis=1).astype(np.float32)
+
+
 def rects256():
     g = synth.rect_map(256, 256)
     bo, D = _scan(61)

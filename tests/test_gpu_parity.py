@@ -286,3 +286,21 @@ def test_work_counts_match_oracle(G, oracle):
     free = np.zeros(parts.shape[0], bool)
     free[inmap] = g[gy[inmap].astype(int), gx[inmap].astype(int)] == 0
     assert w["passed"] == int(free.sum())
+
+
+def test_grid_states_and_warp_latency(G, oracle):
+    """The grid benchmark's states (integer cell centres, headings on exact
+    multiples of 2 pi / N, occupied and border cells included) cast exactly as
+    the oracle; the latency-instrumented cast returns the same ranges and one
+    positive cycle count per warp."""
+    from paper_1705_01167_gb300 import workloads as WL
+    g = synth.rect_map(256, 256)
+    d = G.CDDT(dev(g), 108, 300.0)
+    o = oracle.OracleCDDT(g, 108, 300.0)
+    q = WL.grid_states(256, 256, 3, 108)
+    got = d.calc_range_many(dev(q)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), o.calc_range(q).view(np.uint32))
+    r, cyc = d.calc_range_timed(dev(q))
+    assert np.array_equal(r.cpu().numpy().view(np.uint32), got.view(np.uint32))
+    c = cyc.cpu().numpy()
+    assert c.shape == ((q.shape[0] + 31) // 32,) and (c > 0).all()
