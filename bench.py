@@ -327,8 +327,9 @@ def bench_corridor(args, G, torch, dev, world, rank):
     logw_d = torch.empty(S * P, dtype=torch.float32, device=dev)
     m = G.beam_model(mr)
 
-    def filters_for(handle):
-        return [dict(map=handle, particles=parts_d[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t],
+    def filters_for(handle, parts=None):
+        parts = parts_d if parts is None else parts
+        return [dict(map=handle, particles=parts[t * P:(t + 1) * P], beam_off=bo_d, obs=obs_d[t],
                      model=m, logw=logw_d[t * P:(t + 1) * P], pair_offset=D) for t in range(S)]
 
     plan = G.Plan(filters_for(d))
@@ -356,6 +357,51 @@ def bench_corridor(args, G, torch, dev, world, rank):
     k2 = max(3, args.steps // 2)
     ms_g = timed(plan.launch_graph, k2, 2)
     extra["graph_rays_per_s"] = rays_per_step / (statistics.mean(ms_g) * 1e-3)
+
+    # a full filter step (Section I): the odometry motion model, the sensor
+    # weights of the 200 filters and low-variance resampling, on two particle
+    # buffers that swap roles every step, each direction one CUDA graph
+    rs_m = synth.Stream(synth.SEED_PARTICLES + 77 + RK.seed_offset(rank))
+    seg_d = torch.arange(0, S * P + 1, P, dtype=torch.int64, device=dev)
+    odom_d = torch.from_numpy(np.stack([rs_m.normal(S) * 0.5 + 1.0, rs_m.normal(S) * 0.1,
+                                        rs_m.normal(S) * 0.02], 1).astype(np.float32)).to(dev)
+    noise_d = torch.from_numpy((rs_m.normal(3 * S * P) * 0.05).astype(np.float32).reshape(-1, 3)).to(dev)
+    u0_d = torch.from_numpy(rs_m.uniform(S).astype(np.float32)).to(dev)
+    buf_a = parts_d.clone()
+    buf_b = torch.empty_like(buf_a)
+    scratch_d = torch.empty(S * P, dtype=torch.float64, device=dev)
+    plans_m = [G.Plan(filters_for(d, buf)) for buf in (buf_a, buf_b)]
+    for pl in plans_m:
+        pl.set_shape(**shape)
+        pl.run()
+    graphs = []
+    for src, dst, pl in ((buf_a, buf_b, plans_m[0]), (buf_b, buf_a, plans_m[1])):
+        def mcl_step(src=src, dst=dst, pl=pl):
+            G.motion(src, seg_d, odom_d, noise_d)
+            pl.run()
+            G.resample(src, logw_d, seg_d, u0_d, out=dst, scratch=scratch_d)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            mcl_step()
+        torch.cuda.current_stream().wait_stream(side)
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            mcl_step()
+        graphs.append(gr)
+    flip = [0]
+
+    def mcl():
+        graphs[flip[0]].replay()
+        flip[0] ^= 1
+    ms_m = timed(mcl, k2, 2)
+    extra["mcl_step"] = {"ms": statistics.mean(ms_m),
+                         "rays_per_s": rays_per_step / (statistics.mean(ms_m) * 1e-3),
+                         "steps": "motion model + sensor weights + low-variance resampling of 200 filters x "
+                                  "2500 particles, one CUDA graph"}
+    for pl in plans_m:
+        pl.close()
+    del buf_a, buf_b, scratch_d, noise_d
 
     # the uniform-particle variant (global localization: each filter's
     # particles spread over the whole free space)

@@ -333,6 +333,39 @@ CDDT_API cddt_status cddt_sensor_work(cddt_t h, const float *particles_dev, int6
                              const float *beam_off_dev, int32_t B, int32_t pair_offset,
                              int64_t *out_host, void *stream);
 
+/* ---------------------------------------------------------------- filter steps */
+
+/* The particle filter around the sensor model (Section I: a movement model
+ * from odometry before the sensor model, resampling by belief after it).
+ * The paper gives neither in equations; these are the standard forms (see
+ * each).  Both work on F filters whose particles are consecutive segments of
+ * one array: seg_start_dev int64 [F + 1] (device), non-decreasing, with
+ * segment f = particles [seg_start[f], seg_start[f + 1]) and seg_start[F] =
+ * P.  Random numbers are inputs, so a step is reproducible. */
+
+/* Odometry motion model, in place: particles_dev float [P][3] (x, y, theta);
+ * odom_dev float [F][3] the robot's motion since the last step, (dx, dy) in
+ * its own frame and dtheta; noise_dev float [P][3] a noise sample per
+ * particle (nx, ny, ntheta).  Each pose becomes x + a cos(theta) - b sin(theta),
+ * y + a sin(theta) + b cos(theta), theta + dtheta + ntheta (wrapped into
+ * [0, 2 pi) by one turn), a = dx + nx, b = dy + ny, in float32.
+ * Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_motion(float *particles_dev, int64_t P, const int64_t *seg_start_dev, int32_t F,
+                                 const float *odom_dev, const float *noise_dev, void *stream);
+
+/* Low-variance (systematic) resampling of each filter: weights
+ * w_i = exp(logw_i - max logw) and running sums C_i in double; output
+ * particle m of a filter of n particles is input particle
+ * i = min{ i : C_i > (u0 + m) / n * C_{n-1} } (the last one if none).
+ * particles_dev float [P][3] and logw_dev float [P] (at least one finite
+ * log-weight per filter) in, out_dev float [P][3] (not particles_dev) out,
+ * index_dev int32 [P] (optional, NULL to skip) the chosen input index
+ * within the filter, u0_dev float [F] one uniform offset in [0, 1) per
+ * filter, scratch_dev double [P] the running sums.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_resample(const float *particles_dev, const float *logw_dev, const int64_t *seg_start_dev,
+                                   int32_t F, const float *u0_dev, float *out_dev, int32_t *index_dev,
+                                   double *scratch_dev, void *stream);
+
 /* Measurement helper, no counterpart in the paper: read `sectors` 32-byte
  * sectors of the device buffer buf_dev (32-byte aligned; bytes >= 32, a
  * multiple of 32) at

@@ -202,6 +202,62 @@ def sorted_search_sectors(kb, keys_per_sector: int = 8):
     return out
 
 
+def motion(particles, seg_start, odom, noise) -> np.ndarray:
+    """The odometry motion model around the sensor model (Section I names a
+    movement model from odometry; the standard increment form is the reading
+    used here): each particle moves by the robot's (dx, dy) in its own frame
+    plus its noise sample and turns by dtheta plus noise, theta wrapped into
+    [0, 2 pi) by one turn.  Evaluated in float64 from the float32 inputs and
+    rounded to float32 once.  particles [P, 3], seg_start [F + 1], odom
+    [F, 3], noise [P, 3]."""
+    x = np.asarray(particles, np.float32).astype(np.float64)
+    nz = np.asarray(noise, np.float32).astype(np.float64)
+    od = np.asarray(odom, np.float32).astype(np.float64)
+    seg = np.asarray(seg_start, np.int64)
+    f = np.searchsorted(seg, np.arange(x.shape[0]), side="right") - 1
+    a = od[f, 0] + nz[:, 0]
+    b = od[f, 1] + nz[:, 1]
+    th = x[:, 2]
+    out = np.empty_like(x)
+    out[:, 0] = x[:, 0] + a * np.cos(th) - b * np.sin(th)
+    out[:, 1] = x[:, 1] + a * np.sin(th) + b * np.cos(th)
+    t = th + od[f, 2] + nz[:, 2]
+    two_pi = 2.0 * np.pi
+    t = np.where(t >= two_pi, t - two_pi, np.where(t < 0.0, t + two_pi, t))
+    out[:, 2] = t
+    return out.astype(np.float32)
+
+
+def resample_indices(logw, seg_start, u0):
+    """Low-variance (systematic) resampling of every filter segment (Section
+    I resamples by belief; the low-variance scheme is the reading used here):
+    w_i = exp(logw_i - max logw) and running sums C_i in float64, in index
+    order; output m of a filter of n particles takes the first input i with
+    C_i > (u0 + m) / n * C_{n-1} (the last one when none is).  Returns the
+    within-filter indices [P] and, per output, the distance of its target
+    from the nearest running sum relative to the total (a decision this
+    close may round the other way in another summation order)."""
+    lw = np.asarray(logw, np.float32).astype(np.float64)
+    seg = np.asarray(seg_start, np.int64)
+    u = np.asarray(u0, np.float32).astype(np.float64)
+    idx = np.zeros(lw.shape[0], np.int64)
+    margin = np.zeros(lw.shape[0], np.float64)
+    for f in range(seg.size - 1):
+        a, b = int(seg[f]), int(seg[f + 1])
+        n = b - a
+        if n <= 0:
+            continue
+        w = np.exp(lw[a:b] - lw[a:b].max())
+        C = np.cumsum(w)
+        tot = C[-1]
+        for m in range(n):
+            t = (u[f] + m) / n * tot
+            i = int(np.searchsorted(C, t, side="right"))
+            idx[a + m] = min(i, n - 1)
+            margin[a + m] = np.min(np.abs(C - t)) / tot
+    return idx, margin
+
+
 class OracleCDDT:
     """O2: the plain CDDT built on the CPU (Section IV-A), with query, prune,
     update, beam-model weights and gradient."""

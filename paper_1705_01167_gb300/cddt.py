@@ -30,7 +30,7 @@ EXPORTED = (
     "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
-    "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed",
+    "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -116,6 +116,8 @@ def load(build_if_missing: bool = True):
             "cddt_import": (st, [vp, i32, i32, i32, f32, u32, i32, i64, vp, vp, vp, C.POINTER(vp)]),
             "cddt_gather_probe": (st, [vp, i64, i64, C.c_uint64, vp, vp]),
             "cddt_calc_range_timed": (st, [vp, vp, vp, i64, vp, vp]),
+            "cddt_motion": (st, [vp, i64, vp, i32, vp, vp, vp]),
+            "cddt_resample": (st, [vp, vp, vp, i32, vp, vp, vp, vp, vp]),
             "cddt_export_grid": (st, [vp, vp, vp]),
             "cddt_sensor_work": (st, [vp, vp, i64, vp, i32, i32, vp, vp]),
             "cddt_status_string": (C.c_char_p, [st]),
@@ -446,6 +448,51 @@ def gather_probe(buf: torch.Tensor, sectors: int, seed: int = 1, sink: torch.Ten
         _check(load().cddt_gather_probe(_ptr(buf), buf.numel() * buf.element_size() // 32 * 32, int(sectors),
                                         int(seed), _ptr(sink), _stream(stream)), "cddt_gather_probe")
     return sink
+
+
+def motion(particles: torch.Tensor, seg_start: torch.Tensor, odom: torch.Tensor, noise: torch.Tensor,
+           stream=None) -> torch.Tensor:
+    """``cddt_motion``: odometry motion model, in place on particles [P, 3]
+    (filters are the segments seg_start [F + 1] int64; odom [F, 3]; noise
+    [P, 3])."""
+    _dev(particles, torch.float32, "particles")
+    _dev(seg_start, torch.int64, "seg_start")
+    _dev(odom, torch.float32, "odom")
+    _dev(noise, torch.float32, "noise")
+    P, F = particles.numel() // 3, seg_start.numel() - 1
+    if noise.numel() != 3 * P or odom.numel() != 3 * F or F < 1:
+        raise ValueError("noise must be [P, 3], odom [F, 3] and seg_start [F + 1]")
+    with torch.cuda.device(particles.device):
+        _check(load().cddt_motion(_ptr(particles), P, _ptr(seg_start), F, _ptr(odom), _ptr(noise),
+                                  _stream(stream)), "cddt_motion")
+    return particles
+
+
+def resample(particles: torch.Tensor, logw: torch.Tensor, seg_start: torch.Tensor, u0: torch.Tensor,
+             out: torch.Tensor | None = None, index: torch.Tensor | None = None,
+             scratch: torch.Tensor | None = None, stream=None):
+    """``cddt_resample``: low-variance resampling of every filter segment;
+    returns (out [P, 3], index [P] int32 or None)."""
+    _dev(particles, torch.float32, "particles")
+    _dev(logw, torch.float32, "logw")
+    _dev(seg_start, torch.int64, "seg_start")
+    _dev(u0, torch.float32, "u0")
+    P, F = particles.numel() // 3, seg_start.numel() - 1
+    if logw.numel() != P or u0.numel() != F or F < 1:
+        raise ValueError("logw must be [P], u0 [F] and seg_start [F + 1]")
+    if out is None:
+        out = torch.empty_like(particles)
+    if scratch is None:
+        scratch = torch.empty(max(P, 1), dtype=torch.float64, device=particles.device)
+    _dev(out, torch.float32, "out")
+    _dev(scratch, torch.float64, "scratch")
+    if index is not None:
+        _dev(index, torch.int32, "index")
+    with torch.cuda.device(particles.device):
+        _check(load().cddt_resample(_ptr(particles), _ptr(logw), _ptr(seg_start), F, _ptr(u0), _ptr(out),
+                                    _ptr(index) if index is not None else None, _ptr(scratch), _stream(stream)),
+               "cddt_resample")
+    return out, index
 
 
 class Plan:

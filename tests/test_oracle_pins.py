@@ -625,3 +625,53 @@ def test_sorted_search_sectors_pins():
     got = O.sorted_search_sectors([0, 1, 8, 9, 16, 17, 32, 33, 1000], 8)
     assert list(got) == [1, 2, 2, 3, 3, 4, 4, 5, 9]
     assert list(O.sorted_search_sectors([16, 17], 16)) == [2, 3]
+
+
+def test_motion_model_pins():
+    """The motion model on closed forms: no motion is the identity; a step
+    forward along theta = 0 moves +x, sideways (dy) moves +y; a turn past
+    2 pi wraps by one turn; noise adds to the odometry."""
+    from oracle import oracle as O
+    p = np.array([[10.0, 20.0, 0.0], [5.0, 5.0, 1.0], [7.0, 3.0, 6.2]], np.float32)
+    seg = np.array([0, 3])
+    z = np.zeros((3, 3), np.float32)
+    assert np.array_equal(O.motion(p, seg, np.zeros((1, 3), np.float32), z), p)
+    out = O.motion(p[:1], [0, 1], np.array([[1.0, 0.0, 0.0]], np.float32), z[:1])
+    assert np.allclose(out, [[11.0, 20.0, 0.0]])
+    out = O.motion(p[:1], [0, 1], np.array([[0.0, 2.0, 0.0]], np.float32), z[:1])
+    assert np.allclose(out, [[10.0, 22.0, 0.0]])
+    out = O.motion(p[2:], [0, 1], np.array([[0.0, 0.0, 0.2]], np.float32), z[:1])
+    assert np.isclose(out[0, 2], np.float32(6.2) + np.float32(0.2) - 2 * np.pi, atol=1e-6)
+    nz = np.array([[0.5, -0.25, 0.1]], np.float32)
+    a = O.motion(p[1:2], [0, 1], np.array([[1.0, 1.0, 0.3]], np.float32), nz)
+    b = O.motion(p[1:2], [0, 1], np.array([[1.5, 0.75, 0.4]], np.float32), z[:1])
+    assert np.allclose(a, b, atol=1e-6)
+    th = np.float64(np.float32(1.0))
+    assert np.isclose(a[0, 0], 5.0 + 1.5 * np.cos(th) - 0.75 * np.sin(th), atol=1e-5)
+
+
+def test_resampling_pins():
+    """Systematic resampling: equal weights keep every particle once in
+    order; one finite weight takes every draw; for any weights each particle
+    is drawn floor or ceil of n times its normalised weight, in index order."""
+    from oracle import oracle as O
+    n = 50
+    idx, _ = O.resample_indices(np.full(n, -3.0, np.float32), [0, n], np.array([0.37], np.float32))
+    assert np.array_equal(idx, np.arange(n))
+    lw = np.full(n, -np.inf, np.float32)
+    lw[17] = -5.0
+    idx, _ = O.resample_indices(lw, [0, n], np.array([0.9], np.float32))
+    assert (idx == 17).all()
+    rs = np.random.default_rng(5)
+    lw = rs.normal(-40.0, 3.0, 400).astype(np.float32)
+    seg = np.array([0, 150, 150, 400])
+    u = np.array([0.1, 0.5, 0.99], np.float32)
+    idx, _ = O.resample_indices(lw, seg, u)
+    for f in (0, 2):
+        a, b = seg[f], seg[f + 1]
+        k = idx[a:b]
+        assert (np.diff(k) >= 0).all()
+        w = np.exp(lw[a:b].astype(np.float64) - lw[a:b].max())
+        expect = (b - a) * w / w.sum()
+        cnt = np.bincount(k, minlength=b - a)
+        assert (np.abs(cnt - expect) < 1.0 + 1e-9).all()
