@@ -453,6 +453,26 @@ def bench_corridor(args, G, torch, dev, world, rank):
     extra["warp_latency_cycles"] = lat
     del gq, gout
 
+    # the paper's comparison: a 16-bit lookup table of every state, built on
+    # the GPU from this CDDT; the same sensor model over table reads (all 200
+    # filters in one launch) and the same 10 M sweep
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    lut = G.Lut(d)
+    ev1.record()
+    torch.cuda.synchronize()
+    seg_l = torch.arange(0, S * P + 1, P, dtype=torch.int64, device=dev)
+    ms_lut = timed(lambda: lut.sensor_weights(parts_d, seg_l, bo_d, obs_d, m, logw=logw_d), k2, 2)
+    lut_out = torch.empty(sw.shape[0], dtype=torch.float32, device=dev)
+    ms_lsw = timed(lambda: lut.calc_range_many(sw, out=lut_out), 5, 2)
+    extra["lut"] = {"build_ms": ev0.elapsed_time(ev1), "bytes": lut.info()["bytes"],
+                    "cddt_store_bytes": st0["store_bytes"],
+                    "sensor_rays_per_s": rays_per_step / (statistics.mean(ms_lut) * 1e-3),
+                    "sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_lsw) * 1e-3)}
+    lut.close()
+    del lut_out
+
+
     dp = G.CDDT(grid, w["theta_disc"], mr)
     dp.prune()
     stp = dp.stats()

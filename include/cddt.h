@@ -366,6 +366,41 @@ CDDT_API cddt_status cddt_resample(const float *particles_dev, const float *logw
                                    int32_t F, const float *u0_dev, float *out_dev, int32_t *index_dev,
                                    double *scratch_dev, void *stream);
 
+/* ---------------------------------------------------------------- lookup table */
+
+/* The paper's main comparison (Section II, Table I): a three-dimensional
+ * lookup table of the range of every discrete state (cell centre (i, j),
+ * direction theta_k = 2 pi k / N), 16-bit entries, built on the GPU by casting
+ * every state through a CDDT; queries snap to their state. */
+typedef struct cddt_lut_s *cddt_lut;
+
+/* Build the table of handle h's map, theta_disc N and max_range (its
+ * current store): uint16 [N][H][W], entry = round-half-up(range * scale),
+ * scale = the largest power of two with max_range * scale <= 65535, so the
+ * range read back is code / scale.  2 * W * H * N bytes of device memory,
+ * owned by the table.  Errors: ARG, OOM, CUDA. */
+CDDT_API cddt_status cddt_lut_build(cddt_t h, void *stream, cddt_lut *out);
+CDDT_API cddt_status cddt_lut_destroy(cddt_lut l);
+/* Table bytes and scale; either pointer may be NULL.  Errors: ARG. */
+CDDT_API cddt_status cddt_lut_info(cddt_lut l, int64_t *bytes, float *scale);
+
+/* Ray casts by lookup: pose_dev float [n][3] -> range_dev float [n], the
+ * entry of the query's nearest cell centre and direction index (as
+ * cddt_calc_range_many discretises theta); 0 off the map or for a
+ * non-finite theta.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_lut_calc_range_many(cddt_lut l, const float *pose_dev, float *range_dev, int64_t n,
+                                              void *stream);
+
+/* The fused beam sensor model (as cddt_sensor_weights) over table reads:
+ * F filters as segments of particles_dev float [P][3] (seg_start_dev int64
+ * [F + 1], as cddt_motion), one scan per filter obs_dev float [F][B], shared
+ * beam offsets beam_off_dev float [B]; logw_dev float [P].  Every beam is a
+ * table read (no pairing).  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_lut_sensor_weights(cddt_lut l, const float *particles_dev, int64_t P,
+                                             const int64_t *seg_start_dev, int32_t F, const float *beam_off_dev,
+                                             const float *obs_dev, int32_t B, const cddt_beam_model *m,
+                                             float *logw_dev, void *stream);
+
 /* Measurement helper, no counterpart in the paper: read `sectors` 32-byte
  * sectors of the device buffer buf_dev (32-byte aligned; bytes >= 32, a
  * multiple of 32) at

@@ -202,6 +202,62 @@ def sorted_search_sectors(kb, keys_per_sector: int = 8):
     return out
 
 
+def lut_scale(max_range: float) -> float:
+    """The 16-bit table's scale (reading L1): the largest power of two s
+    with max_range * s <= 65535, so code = round-half-up(range * s) fits and
+    code / s is exact."""
+    s = 1.0
+    while max_range * s * 2.0 <= 65535.0:
+        s *= 2.0
+    while max_range * s > 65535.0:
+        s /= 2.0
+    return s
+
+
+def lut_table(params, grid, max_range: float) -> np.ndarray:
+    """The paper's three-dimensional lookup table (Section II, 16-bit entries,
+    Table I): the O4 range of every discrete state (cell centre, theta_k),
+    coded as round-half-up(range * scale) in float32, clamped to 65535."""
+    r = params.lut(grid)
+    sc = np.float32(lut_scale(max_range))
+    code = np.floor(r * sc + np.float32(0.5))
+    return np.clip(code, 0, 65535).astype(np.uint16)
+
+
+def lut_lookup(params, table, max_range: float, poses) -> np.ndarray:
+    """A query read from the table: its nearest cell centre (floor(x + 1/2),
+    floor(y + 1/2) in float32; off the map gives 0) and its direction index
+    (as the CDDT's query, S1), code / scale."""
+    q = np.asarray(poses, np.float32).reshape(-1, 3)
+    N, H, W = table.shape
+    inv = np.float32(1.0 / lut_scale(max_range))
+    out = np.zeros(q.shape[0], np.float32)
+    for n in range(q.shape[0]):
+        fx = np.floor(q[n, 0] + np.float32(0.5))
+        fy = np.floor(q[n, 1] + np.float32(0.5))
+        if not (0 <= fx < W and 0 <= fy < H):
+            continue
+        k = params.query_k(float(q[n, 2]))
+        if k < 0:
+            continue
+        out[n] = np.float32(table[k, int(fy), int(fx)]) * inv
+    return out
+
+
+def lut_sensor_weights(params, table, max_range: float, particles, beam_off, obs, model) -> np.ndarray:
+    """log w of each particle over table reads: the beam model (S9, float64)
+    of every beam's looked-up range, summed."""
+    q = np.asarray(particles, np.float32).reshape(-1, 3)
+    bo = np.asarray(beam_off, np.float32)
+    B = bo.size
+    dirs = (q[:, 2:3] + bo[None, :]).astype(np.float32)
+    poses = np.concatenate([np.repeat(q[:, :2], B, 0), dirs.reshape(-1, 1)], 1)
+    r = lut_lookup(params, table, max_range, poses).astype(np.float64)
+    z = np.tile(np.asarray(obs, np.float32).astype(np.float64), q.shape[0])
+    p, _ = beam_eval(model, z, r)
+    return np.log(p).reshape(-1, B).sum(1)
+
+
 def motion(particles, seg_start, odom, noise) -> np.ndarray:
     """The odometry motion model around the sensor model (Section I names a
     movement model from odometry; the standard increment form is the reading

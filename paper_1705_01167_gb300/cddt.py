@@ -31,6 +31,7 @@ EXPORTED = (
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
     "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
+    "cddt_lut_build", "cddt_lut_destroy", "cddt_lut_info", "cddt_lut_calc_range_many", "cddt_lut_sensor_weights",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -117,6 +118,11 @@ def load(build_if_missing: bool = True):
             "cddt_gather_probe": (st, [vp, i64, i64, C.c_uint64, vp, vp]),
             "cddt_calc_range_timed": (st, [vp, vp, vp, i64, vp, vp]),
             "cddt_motion": (st, [vp, i64, vp, i32, vp, vp, vp]),
+            "cddt_lut_build": (st, [vp, vp, C.POINTER(vp)]),
+            "cddt_lut_destroy": (st, [vp]),
+            "cddt_lut_info": (st, [vp, C.POINTER(i64), C.POINTER(f32)]),
+            "cddt_lut_calc_range_many": (st, [vp, vp, vp, i64, vp]),
+            "cddt_lut_sensor_weights": (st, [vp, vp, i64, vp, i32, vp, vp, i32, C.POINTER(BeamModel), vp, vp]),
             "cddt_resample": (st, [vp, vp, vp, i32, vp, vp, vp, vp, vp]),
             "cddt_export_grid": (st, [vp, vp, vp]),
             "cddt_sensor_work": (st, [vp, vp, i64, vp, i32, i32, vp, vp]),
@@ -448,6 +454,61 @@ def gather_probe(buf: torch.Tensor, sectors: int, seed: int = 1, sink: torch.Ten
         _check(load().cddt_gather_probe(_ptr(buf), buf.numel() * buf.element_size() // 32 * 32, int(sectors),
                                         int(seed), _ptr(sink), _stream(stream)), "cddt_gather_probe")
     return sink
+
+
+class Lut:
+    """``cddt_lut_*``: the paper's 3D lookup table of every discrete state's
+    range (16-bit), built from a CDDT; queries snap to their state."""
+
+    def __init__(self, cddt: "CDDT", stream=None):
+        h = C.c_void_p()
+        with torch.cuda.device(cddt.device):
+            _check(load().cddt_lut_build(cddt.handle, _stream(stream), C.byref(h)), "cddt_lut_build")
+        self._h = h
+        self.device = cddt.device
+
+    def info(self):
+        b, sc = C.c_int64(), C.c_float()
+        _check(load().cddt_lut_info(self._h, C.byref(b), C.byref(sc)), "cddt_lut_info")
+        return {"bytes": b.value, "scale": sc.value}
+
+    def calc_range_many(self, poses: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        _dev(poses, torch.float32, "poses")
+        n = poses.numel() // 3
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=poses.device)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_lut_calc_range_many(self._h, _ptr(poses), _ptr(out), n, _stream(stream)),
+                   "cddt_lut_calc_range_many")
+        return out
+
+    def sensor_weights(self, particles, seg_start, beam_off, obs, model: BeamModel, logw=None, stream=None):
+        """obs [F, B] (one scan per filter segment of particles)."""
+        _dev(particles, torch.float32, "particles")
+        _dev(seg_start, torch.int64, "seg_start")
+        _dev(beam_off, torch.float32, "beam_off")
+        _dev(obs, torch.float32, "obs")
+        P, F, B = particles.numel() // 3, seg_start.numel() - 1, beam_off.numel()
+        if obs.numel() != F * B:
+            raise ValueError("obs must be [F, B]")
+        if logw is None:
+            logw = torch.empty(P, dtype=torch.float32, device=particles.device)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_lut_sensor_weights(self._h, _ptr(particles), P, _ptr(seg_start), F, _ptr(beam_off),
+                                                  _ptr(obs), B, C.byref(model), _ptr(logw), _stream(stream)),
+                   "cddt_lut_sensor_weights")
+        return logw
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cddt_lut_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def motion(particles: torch.Tensor, seg_start: torch.Tensor, odom: torch.Tensor, noise: torch.Tensor,

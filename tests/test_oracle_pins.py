@@ -675,3 +675,25 @@ def test_resampling_pins():
         expect = (b - a) * w / w.sum()
         cnt = np.bincount(k, minlength=b - a)
         assert (np.abs(cnt - expect) < 1.0 + 1e-9).all()
+
+
+def test_lookup_table_pins(oracle):
+    """The 16-bit table: its scale is the largest power of two that fits
+    max_range in 16 bits; entries code the O4 ranges exactly up to half a
+    step; a lookup at a cell centre in a table direction returns that
+    entry, and snaps any pose inside the cell to it."""
+    from oracle import oracle as O
+    assert O.lut_scale(1000.0) == 64.0 and O.lut_scale(300.0) == 128.0 and O.lut_scale(65535.0) == 1.0
+    g = synth.rect_map(48, 40, n_rects=5, seed=9)
+    N, mr = 24, 80.0
+    d = oracle.OracleCDDT(g, N, mr)
+    tab = O.lut_table(d.params, g, mr)
+    ref = d.params.lut(g)
+    sc = O.lut_scale(mr)
+    assert np.all(np.abs(tab / sc - ref) <= 0.5 / sc + 1e-6)
+    k, j, i = 5, 17, 23
+    th = np.float32(2.0 * np.pi * k / N)
+    poses = np.array([[i, j, th], [i + 0.3, j - 0.45, th], [-3.0, 2.0, th]], np.float32)
+    got = O.lut_lookup(d.params, tab, mr, poses)
+    assert got[0] == np.float32(tab[k, j, i]) / np.float32(sc) == got[1]
+    assert got[2] == 0.0
