@@ -472,6 +472,22 @@ def bench_corridor(args, G, torch, dev, world, rank):
     lut.close()
     del lut_out
 
+    # the Bresenham baseline (Section II's BL) on the same 10 M sweep and on
+    # the tracking filter's rays (every particle x beam as a query), against
+    # the CDDT's plain ray cast of the same rays
+    bl_out = torch.empty(sw.shape[0], dtype=torch.float32, device=dev)
+    ms_bl = timed(lambda: d.cast_bresenham(sw, out=bl_out), 3, 1)
+    fr = torch.cat([parts_d[:, :2].repeat_interleave(B, 0),
+                    (parts_d[:, 2:3] + bo_d[None, :]).reshape(-1, 1)], 1).contiguous()
+    fr_out = torch.empty(fr.shape[0], dtype=torch.float32, device=dev)
+    ms_blf = timed(lambda: d.cast_bresenham(fr, out=fr_out), 3, 1)
+    ms_cf = timed(lambda: d.calc_range_many(fr, out=fr_out), 3, 1)
+    extra["bresenham"] = {"sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_bl) * 1e-3),
+                          "filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_blf) * 1e-3),
+                          "cddt_filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_cf) * 1e-3)}
+    del bl_out, fr, fr_out
+
+
 
     dp = G.CDDT(grid, w["theta_disc"], mr)
     dp.prune()

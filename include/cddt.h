@@ -366,6 +366,21 @@ CDDT_API cddt_status cddt_resample(const float *particles_dev, const float *logw
                                    int32_t F, const float *u0_dev, float *out_dev, int32_t *index_dev,
                                    double *scratch_dev, void *stream);
 
+/* ---------------------------------------------------------------- baselines */
+
+/* The Bresenham line caster of Section II (the paper's BL baseline) over the
+ * handle's grid and max_range: pose_dev float [n][3] -> range_dev float [n].
+ * The walk runs over the digital line from the query's cell floor(p + 1/2)
+ * to floor(p + max_range (cos theta, sin theta) + 1/2) (double precision) and
+ * stops at the first occupied cell; the range is the distance from the query
+ * point to that cell's centre, clamped to max_range; 0 from an occupied or
+ * off-map cell or a non-finite heading; max_range when the walk leaves the
+ * map or reaches its end
+ * without a hit.  Its cost grows with the free distance along the ray (the
+ * long tail the paper measures).  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_cast_bresenham(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
+                                         void *stream);
+
 /* ---------------------------------------------------------------- lookup table */
 
 /* The paper's main comparison (Section II, Table I): a three-dimensional

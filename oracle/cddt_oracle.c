@@ -583,6 +583,7 @@ void oc_cast_bresenham(const uint8_t *grid, int32_t W, int32_t H, const double *
 {
     for (int64_t q = 0; q < n; ++q) {
         double x = pose[3 * q], y = pose[3 * q + 1], th = pose[3 * q + 2];
+        if (!isfinite(th) || !isfinite(x) || !isfinite(y)) { out[q] = 0.0; continue; }  /* as a query (S6) */
         long x0 = (long)floor(x + 0.5), y0 = (long)floor(y + 0.5);
         if (x0 < 0 || x0 >= W || y0 < 0 || y0 >= H || grid[(int64_t)y0 * W + x0]) { out[q] = 0.0; continue; }
         long x1 = (long)floor(x + max_range * cos(th) + 0.5);

@@ -32,6 +32,7 @@ EXPORTED = (
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
     "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
     "cddt_lut_build", "cddt_lut_destroy", "cddt_lut_info", "cddt_lut_calc_range_many", "cddt_lut_sensor_weights",
+    "cddt_cast_bresenham",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -119,6 +120,7 @@ def load(build_if_missing: bool = True):
             "cddt_calc_range_timed": (st, [vp, vp, vp, i64, vp, vp]),
             "cddt_motion": (st, [vp, i64, vp, i32, vp, vp, vp]),
             "cddt_lut_build": (st, [vp, vp, C.POINTER(vp)]),
+            "cddt_cast_bresenham": (st, [vp, vp, vp, i64, vp]),
             "cddt_lut_destroy": (st, [vp]),
             "cddt_lut_info": (st, [vp, C.POINTER(i64), C.POINTER(f32)]),
             "cddt_lut_calc_range_many": (st, [vp, vp, vp, i64, vp]),
@@ -352,6 +354,17 @@ class CDDT:
         if particles.numel() != 3 * P or obs.numel() != B:
             raise ValueError("particles must be [P, 3] and obs [B] like beam_off")
         return P, B
+
+    def cast_bresenham(self, poses: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """``cddt_cast_bresenham``: the Bresenham baseline caster on this map."""
+        _dev(poses, torch.float32, "poses")
+        n = poses.numel() // 3
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=poses.device)
+        with torch.cuda.device(self.device):
+            _check(load().cddt_cast_bresenham(self._h, _ptr(poses), _ptr(out), n, _stream(stream)),
+                   "cddt_cast_bresenham")
+        return out
 
     def calc_range_timed(self, poses: torch.Tensor, stream=None):
         """``cddt_calc_range_timed``: (ranges [n], SM cycles of each warp of 32

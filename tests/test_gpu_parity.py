@@ -304,3 +304,15 @@ def test_grid_states_and_warp_latency(G, oracle):
     assert np.array_equal(r.cpu().numpy().view(np.uint32), got.view(np.uint32))
     c = cyc.cpu().numpy()
     assert c.shape == ((q.shape[0] + 31) // 32,) and (c > 0).all()
+
+
+def test_bresenham_baseline_matches_oracle(G, oracle):
+    """The GPU Bresenham baseline caster walks the same digital lines as the
+    oracle's (double-precision end points, integer stepping)."""
+    g = synth.rect_map(256, 256)
+    d = G.CDDT(dev(g), 108, 300.0)
+    q = gc.random_queries(256, 256, 20000, 31)
+    q[:4] = [[-2.0, 10.0, 0.5], [10.0, 10.0, np.nan], [100.2, 50.7, 0.0], [255.4, 255.4, 0.785398]]
+    got = d.cast_bresenham(dev(q)).cpu().numpy()
+    want = oracle.cast_bresenham(g, q.astype(np.float64), 300.0).astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
