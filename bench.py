@@ -485,7 +485,28 @@ def bench_corridor(args, G, torch, dev, world, rank):
     extra["bresenham"] = {"sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_bl) * 1e-3),
                           "filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_blf) * 1e-3),
                           "cddt_filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_cf) * 1e-3)}
-    del bl_out, fr, fr_out
+
+    # the ray marching baseline (Section II's RM): its distance transform's
+    # build, the same sweep and filter rays, and the distance reads per ray
+    # of the sweep (the long tail the paper describes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rm = G.RayMarch(d)
+    torch.cuda.synchronize()
+    rm_build_ms = (time.perf_counter() - t0) * 1e3
+    ms_rm = timed(lambda: rm.calc_range_many(sw, out=bl_out), 3, 1)
+    ms_rmf = timed(lambda: rm.calc_range_many(fr, out=fr_out), 3, 1)
+    rm_steps = torch.empty(sw.shape[0], dtype=torch.int32, device=dev)
+    rm.calc_range_many(sw, out=bl_out, steps=rm_steps)
+    st_f = rm_steps.float()
+    extra["raymarch"] = {"sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_rm) * 1e-3),
+                         "filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_rmf) * 1e-3),
+                         "build_ms": rm_build_ms, "transform_bytes": 4 * grid.shape[0] * grid.shape[1],
+                         "sweep_reads_mean": float(st_f.mean()),
+                         "sweep_reads_p99": float(torch.quantile(st_f[:1 << 20], 0.99)),
+                         "sweep_reads_max": int(rm_steps.max())}
+    rm.close()
+    del bl_out, fr, fr_out, rm_steps, st_f
 
 
 

@@ -371,15 +371,51 @@ CDDT_API cddt_status cddt_resample(const float *particles_dev, const float *logw
 /* The Bresenham line caster of Section II (the paper's BL baseline) over the
  * handle's grid and max_range: pose_dev float [n][3] -> range_dev float [n].
  * The walk runs over the digital line from the query's cell floor(p + 1/2)
- * to floor(p + max_range (cos theta, sin theta) + 1/2) (double precision) and
- * stops at the first occupied cell; the range is the distance from the query
- * point to that cell's centre, clamped to max_range; 0 from an occupied or
- * off-map cell or a non-finite heading; max_range when the walk leaves the
- * map or reaches its end
- * without a hit.  Its cost grows with the free distance along the ray (the
- * long tail the paper measures).  Errors: ARG, CUDA. */
+ * to floor(p + max_range (c, s) + 1/2) and stops at the first occupied cell;
+ * (c, s) is the heading's direction by the baseline rule (float32: the
+ * remainder modulo pi/2 in three fused parts, Taylor polynomials to degree
+ * 9 and 10, within 2 ulp), the end point one fused multiply-add per
+ * coordinate.  The range is the float32 distance from the query point to
+ * the hit cell's centre, clamped to max_range; 0 from an occupied or
+ * off-map cell or a non-finite coordinate; max_range when the walk leaves
+ * the map or reaches its end without a hit.  Its cost grows with the free
+ * distance along the ray (the long tail the paper measures).
+ * Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_cast_bresenham(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
                                          void *stream);
+
+/* The ray marching caster of Section II (the paper's RM baseline): a
+ * Euclidean distance transform of the handle's grid, precomputed once, and a
+ * march that advances each ray by the transform's value at the cell it
+ * stands on.  The transform is a snapshot: after cddt_update the caller
+ * builds a new one (the precomputation the paper names as ray marching's
+ * cost on a changing map). */
+typedef struct cddt_rm_s *cddt_rm;
+
+/* Build the transform of handle h's current grid: float [H][W], cell (i, j)
+ * at j * W + i holds the distance between its centre and the nearest
+ * occupied cell's centre, the square root (double, rounded to float) of an
+ * exact integer squared distance; W + H everywhere on a map without an
+ * occupied cell.  4 * W * H bytes of device memory owned by the object, plus
+ * 2 * W * H bytes of scratch during the build (stream-ordered).  Keeps h's
+ * max_range.  Errors: ARG (NULL, or h not on the current device), OOM, CUDA. */
+CDDT_API cddt_status cddt_rm_build(cddt_t h, void *stream, cddt_rm *out);
+CDDT_API cddt_status cddt_rm_destroy(cddt_rm r);
+/* The transform's device pointer (owned by r, valid until destroy) and its
+ * size in bytes; either out-pointer may be NULL.  Errors: ARG. */
+CDDT_API cddt_status cddt_rm_distances(cddt_rm r, const float **dist_dev, int64_t *bytes);
+
+/* Ray casts by marching: pose_dev float [n][3] -> range_dev float [n];
+ * steps_dev int32 [n] (optional, NULL to skip) the transform reads of each
+ * ray.  With (c, s) the heading's direction by the baseline rule (as
+ * cddt_cast_bresenham) and t = 0, each sample reads the cell floor(fma(t, (c, s), (x, y)) + 1/2): off the
+ * map ends the ray at max_range, a zero distance (an occupied cell) returns
+ * t, otherwise t += distance, and t >= max_range returns max_range.  0 from
+ * an occupied or off-map cell or a non-finite coordinate.  The returned
+ * sample lies in an occupied cell, at or beyond the ray's true first
+ * contact; a ray that grazes a corner can step past it.  Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_rm_calc_range_many(cddt_rm r, const float *pose_dev, float *range_dev,
+                                             int32_t *steps_dev, int64_t n, void *stream);
 
 /* ---------------------------------------------------------------- lookup table */
 

@@ -13,8 +13,9 @@
  *       construction algorithm (Section IV-A), each bin sorted afterwards,
  *       queried with a textbook successor / predecessor binary search
  *       (Section IV-B, Section IV-C)
- *   O3  exact voxel-traversal caster (Amanatides & Woo, 1987) and a
- *       Bresenham caster (Section II), for approximation reports only
+ *   O3  exact voxel-traversal caster (Amanatides & Woo, 1987), a
+ *       Bresenham caster and a ray marcher over a distance transform
+ *       (Section II), for approximation reports and the baselines
  *   O4  tiny-map lookup table, every discrete state cast by O1 (Section II)
  *   O5  FP64 beam sensor model, its log-weight and its analytic gradient
  *   prune (Section IV-C) and incremental update (Section IV-D)
@@ -578,33 +579,118 @@ void oc_cast_exact(const uint8_t *grid, int32_t W, int32_t H, const double *pose
 
 /* Bresenham's line (Section II): integer steps from the query cell toward the
  * point max_range away; Euclidean distance to the first occupied pixel. */
-void oc_cast_bresenham(const uint8_t *grid, int32_t W, int32_t H, const double *pose, int64_t n,
-                       double max_range, double *out)
+/* Direction of a continuous heading for the Bresenham and ray marching
+ * casters (reading D1), float32, one rounding per operation:
+ *   1. |theta| > 2^16: theta = fmodf(theta, fl(2 pi))   (exact remainder)
+ *   2. j = rint(theta * fl(2/pi)); r = theta - j pi/2, with pi/2 split into
+ *      three floats P1 + P2 + P3 and one fused multiply-add per part
+ *      (Cody & Waite's additive reduction)
+ *   3. sin r = r + r^3 (-1/3! + r^2 (1/5! + r^2 (-1/7! + r^2 / 9!))),
+ *      cos r = 1 + r^2 (-1/2! + r^2 (1/4! + r^2 (-1/6! + r^2 (1/8! - r^2 / 10!)))),
+ *      each bracket one fused multiply-add, coefficients fl(1/n!)
+ *   4. quadrant j mod 4: (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s). */
+void oc_dir_sincos(float th, float *sin_out, float *cos_out)
+{
+    const float P1 = 0x1.921fb6p+0f, P2 = -0x1.777a5cp-25f, P3 = -0x1.ee59dap-50f;
+    if (fabsf(th) > 65536.0f) th = fmodf(th, 0x1.921fb6p+2f);
+    float j = rintf(th * 0x1.45f306p-1f);
+    float r = fmaf(-j, P1, th);
+    r = fmaf(-j, P2, r);
+    r = fmaf(-j, P3, r);
+    float r2 = r * r;
+    float sp = fmaf(fmaf(fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f), r2, 1.0f / 120.0f), r2, -1.0f / 6.0f);
+    float sr = fmaf(r2 * r, sp, r);
+    float cp = fmaf(r2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    cp = fmaf(r2, cp, -1.0f / 720.0f);
+    cp = fmaf(r2, cp, 1.0f / 24.0f);
+    cp = fmaf(r2, cp, -0.5f);
+    float cr = fmaf(r2, cp, 1.0f);
+    switch ((int)j & 3) {
+    case 0: *sin_out = sr; *cos_out = cr; break;
+    case 1: *sin_out = cr; *cos_out = -sr; break;
+    case 2: *sin_out = -sr; *cos_out = -cr; break;
+    default: *sin_out = -cr; *cos_out = sr; break;
+    }
+}
+
+/* Bresenham's line caster (Section II), float32 query and arithmetic: the
+ * digital line from the query's cell floor(p + 1/2) to the cell
+ * floor(p + max_range (c, s) + 1/2) (one fused multiply-add per coordinate;
+ * c, s by oc_dir_sincos) by integer error stepping; the range is the
+ * distance from the query point to the first occupied cell's centre, at
+ * most max_range.  0 for a non-finite coordinate or a start cell that is
+ * occupied or off the map (as a CDDT query, S6); max_range when the walk
+ * leaves the map or reaches its end. */
+void oc_cast_bresenham(const uint8_t *grid, int32_t W, int32_t H, const float *pose, int64_t n, float max_range,
+                       float *out)
 {
     for (int64_t q = 0; q < n; ++q) {
-        double x = pose[3 * q], y = pose[3 * q + 1], th = pose[3 * q + 2];
-        if (!isfinite(th) || !isfinite(x) || !isfinite(y)) { out[q] = 0.0; continue; }  /* as a query (S6) */
-        long x0 = (long)floor(x + 0.5), y0 = (long)floor(y + 0.5);
-        if (x0 < 0 || x0 >= W || y0 < 0 || y0 >= H || grid[(int64_t)y0 * W + x0]) { out[q] = 0.0; continue; }
-        long x1 = (long)floor(x + max_range * cos(th) + 0.5);
-        long y1 = (long)floor(y + max_range * sin(th) + 0.5);
-        long ddx = labs(x1 - x0), ddy = -labs(y1 - y0);
+        float x = pose[3 * q], y = pose[3 * q + 1], th = pose[3 * q + 2];
+        if (!isfinite(th) || !isfinite(x) || !isfinite(y)) { out[q] = 0.0f; continue; }
+        float fx0 = floorf(x + 0.5f), fy0 = floorf(y + 0.5f);
+        if (!(fx0 >= 0.0f && fx0 < (float)W && fy0 >= 0.0f && fy0 < (float)H) ||
+            grid[(int64_t)fy0 * W + (int64_t)fx0]) { out[q] = 0.0f; continue; }
+        float s, c;
+        oc_dir_sincos(th, &s, &c);
+        long long x0 = (long long)fx0, y0 = (long long)fy0;
+        long long x1 = (long long)floorf(fmaf(max_range, c, x) + 0.5f);
+        long long y1 = (long long)floorf(fmaf(max_range, s, y) + 0.5f);
+        long long ddx = llabs(x1 - x0), ddy = -llabs(y1 - y0);
         int sx = x0 < x1 ? 1 : -1, sy = y0 < y1 ? 1 : -1;
-        long err = ddx + ddy;
-        double res = max_range;
-        long cx = x0, cy = y0;
+        long long err = ddx + ddy, cx = x0, cy = y0;
+        float res = max_range;
         while (!(cx == x1 && cy == y1)) {
-            long e2 = 2 * err;
+            long long e2 = 2 * err;
             if (e2 >= ddy) { err += ddy; cx += sx; }
             if (e2 <= ddx) { err += ddx; cy += sy; }
             if (cx < 0 || cx >= W || cy < 0 || cy >= H) break;
             if (grid[(int64_t)cy * W + cx]) {
-                res = sqrt((cx - x) * (cx - x) + (cy - y) * (cy - y));
+                float dx = (float)cx - x, dy = (float)cy - y;
+                res = sqrtf(dx * dx + dy * dy);
                 if (res > max_range) res = max_range;
                 break;
             }
         }
         out[q] = res;
+    }
+}
+
+/* Ray marching (Section II, reading RM1) over a distance transform E, float
+ * [H][W], E[j*W + i] the distance from cell (i, j)'s centre to the nearest
+ * occupied cell's centre (0 on occupied cells).  float32 throughout, the
+ * sample point by explicit fmaf: from t = 0, read the cell under
+ * (x + t c, y + t s); stop off the map (max_range) or on an occupied cell
+ * (t); else advance t by the distance read, stopping at max_range.  c, s
+ * come from oc_dir_sincos.  0 for a non-finite
+ * coordinate or a start off the map.  steps[q] = distance reads of ray q. */
+void oc_raymarch(const float *E, int32_t W, int32_t H, const float *pose, int64_t n, float max_range,
+                 float *out, int32_t *steps)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        float x = pose[3 * q], y = pose[3 * q + 1], th = pose[3 * q + 2];
+        float res = 0.0f;
+        int32_t reads = 0;
+        if (isfinite(x) && isfinite(y) && isfinite(th)) {
+            float fx = floorf(x + 0.5f), fy = floorf(y + 0.5f);
+            if (fx >= 0.0f && fx < (float)W && fy >= 0.0f && fy < (float)H) {
+                float s, c;
+                oc_dir_sincos(th, &s, &c);
+                float t = 0.0f;
+                res = max_range;
+                for (;;) {
+                    fx = floorf(fmaf(t, c, x) + 0.5f);
+                    fy = floorf(fmaf(t, s, y) + 0.5f);
+                    if (!(fx >= 0.0f && fx < (float)W && fy >= 0.0f && fy < (float)H)) break;
+                    float d = E[(int64_t)fy * W + (int64_t)fx];
+                    ++reads;
+                    if (d == 0.0f) { res = t; break; }
+                    t = t + d;
+                    if (!(t < max_range)) break;
+                }
+            }
+        }
+        out[q] = res;
+        steps[q] = reads;
     }
 }
 

@@ -78,7 +78,9 @@ def lib():
                 "oc_bin_brute": (i32, [vp, vp, i32, i32, vp, i32]),
                 "oc_lut": (None, [vp, vp, vp]),
                 "oc_cast_exact": (None, [vp, i32, i32, vp, i64, f64, i32, vp]),
-                "oc_cast_bresenham": (None, [vp, i32, i32, vp, i64, f64, vp]),
+                "oc_cast_bresenham": (None, [vp, i32, i32, vp, i64, f32, vp]),
+                "oc_dir_sincos": (None, [f32, vp, vp]),
+                "oc_raymarch": (None, [vp, i32, i32, vp, i64, f32, vp, vp]),
                 "oc_beam_eval": (None, [vp, vp, vp, i64, vp, vp]),
                 "oc_sensor_weights": (None, [vp, vp, i64, vp, vp, i32, vp, vp, vp, i32]),
                 "oc_sensor_grad": (None, [vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, i32]),
@@ -442,12 +444,59 @@ def cast_exact(grid, poses, max_range: float, mode: int = 0) -> np.ndarray:
 
 
 def cast_bresenham(grid, poses, max_range: float) -> np.ndarray:
+    """Bresenham's line caster (Section II), float32 poses -> float32 ranges."""
     g = _u8(grid)
     H, W = g.shape
-    q = np.ascontiguousarray(poses, np.float64).reshape(-1, 3)
-    out = np.empty(q.shape[0], np.float64)
-    lib().oc_cast_bresenham(_p(g), W, H, _p(q), q.shape[0], max_range, _p(out))
+    q = np.ascontiguousarray(poses, np.float32).reshape(-1, 3)
+    out = np.empty(q.shape[0], np.float32)
+    lib().oc_cast_bresenham(_p(g), W, H, _p(q), q.shape[0], float(np.float32(max_range)), _p(out))
     return out
+
+
+def dir_sincos(theta) -> tuple[np.ndarray, np.ndarray]:
+    """(sin, cos) of float32 headings by the baseline casters' direction rule
+    (reading D1)."""
+    th = np.ascontiguousarray(theta, np.float32).reshape(-1)
+    s = np.empty_like(th)
+    c = np.empty_like(th)
+    fs, fc = C.c_float(), C.c_float()
+    fn = lib().oc_dir_sincos
+    for i, t in enumerate(th.tolist()):
+        fn(t, C.byref(fs), C.byref(fc))
+        s[i], c[i] = fs.value, fc.value
+    return s, c
+
+
+def edt(grid) -> np.ndarray:
+    """Euclidean distance transform for ray marching (Section II, reading
+    RM1): float32 [H, W], each cell's distance from its centre to the nearest
+    occupied cell's centre, sqrt of the exact integer squared distance taken
+    in float64 and rounded to float32; W + H everywhere on a map with no
+    occupied cell.  The nearest occupied cell comes from scipy's exact
+    transform (its indices; the distance itself is recomputed here in
+    integers)."""
+    from scipy import ndimage
+
+    occ = _u8(grid) != 0
+    H, W = occ.shape
+    if not occ.any():
+        return np.full((H, W), np.float32(W + H), np.float32)
+    idx = ndimage.distance_transform_edt(~occ, return_distances=False, return_indices=True)
+    jj, ii = np.mgrid[0:H, 0:W]
+    d2 = (jj - idx[0]).astype(np.int64) ** 2 + (ii - idx[1]).astype(np.int64) ** 2
+    return np.sqrt(d2.astype(np.float64)).astype(np.float32)
+
+
+def raymarch(dist, poses, max_range: float):
+    """Ray marching over the transform ``dist`` (Section II, reading RM1):
+    (ranges float32 [n], distance reads int32 [n])."""
+    E = np.ascontiguousarray(dist, np.float32)
+    H, W = E.shape
+    q = np.ascontiguousarray(poses, np.float32).reshape(-1, 3)
+    out = np.empty(q.shape[0], np.float32)
+    steps = np.empty(q.shape[0], np.int32)
+    lib().oc_raymarch(_p(E), W, H, _p(q), q.shape[0], float(np.float32(max_range)), _p(out), _p(steps))
+    return out, steps
 
 
 def openmp_threads() -> int:

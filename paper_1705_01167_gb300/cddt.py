@@ -32,7 +32,7 @@ EXPORTED = (
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
     "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
     "cddt_lut_build", "cddt_lut_destroy", "cddt_lut_info", "cddt_lut_calc_range_many", "cddt_lut_sensor_weights",
-    "cddt_cast_bresenham",
+    "cddt_cast_bresenham", "cddt_rm_build", "cddt_rm_destroy", "cddt_rm_distances", "cddt_rm_calc_range_many",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -121,6 +121,10 @@ def load(build_if_missing: bool = True):
             "cddt_motion": (st, [vp, i64, vp, i32, vp, vp, vp]),
             "cddt_lut_build": (st, [vp, vp, C.POINTER(vp)]),
             "cddt_cast_bresenham": (st, [vp, vp, vp, i64, vp]),
+            "cddt_rm_build": (st, [vp, vp, C.POINTER(vp)]),
+            "cddt_rm_destroy": (st, [vp]),
+            "cddt_rm_distances": (st, [vp, C.POINTER(vp), C.POINTER(i64)]),
+            "cddt_rm_calc_range_many": (st, [vp, vp, vp, vp, i64, vp]),
             "cddt_lut_destroy": (st, [vp]),
             "cddt_lut_info": (st, [vp, C.POINTER(i64), C.POINTER(f32)]),
             "cddt_lut_calc_range_many": (st, [vp, vp, vp, i64, vp]),
@@ -515,6 +519,63 @@ class Lut:
     def close(self):
         if getattr(self, "_h", None):
             load().cddt_lut_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RayMarch:
+    """``cddt_rm_*``: the paper's ray marching baseline, a Euclidean distance
+    transform of a CDDT's grid (a snapshot at construction) and a caster that
+    steps each ray by it."""
+
+    def __init__(self, cddt: "CDDT", stream=None):
+        h = C.c_void_p()
+        with torch.cuda.device(cddt.device):
+            _check(load().cddt_rm_build(cddt.handle, _stream(stream), C.byref(h)), "cddt_rm_build")
+        self._h = h
+        self.device = cddt.device
+        self.shape = (cddt.H, cddt.W)
+
+    def distances(self) -> torch.Tensor:
+        """A copy of the transform, float32 [H, W]."""
+        p, b = C.c_void_p(), C.c_int64()
+        _check(load().cddt_rm_distances(self._h, C.byref(p), C.byref(b)), "cddt_rm_distances")
+        if b.value != 4 * self.shape[0] * self.shape[1]:
+            raise RuntimeError("cddt_rm_distances: unexpected size")
+
+        class _View:  # the object's own buffer, seen through the CUDA array interface
+            __cuda_array_interface__ = {"shape": self.shape, "typestr": "<f4", "data": (p.value, False),
+                                        "strides": None, "version": 3}
+
+        with torch.cuda.device(self.device):
+            return torch.as_tensor(_View(), device=self.device).clone()
+
+    def calc_range_many(self, poses: torch.Tensor, out: torch.Tensor | None = None,
+                        steps: torch.Tensor | None = None, stream=None):
+        """Ranges [n] (and, into ``steps`` int32 [n] when given, the reads of
+        each ray)."""
+        _dev(poses, torch.float32, "poses")
+        n = poses.numel() // 3
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=poses.device)
+        if steps is not None:
+            _dev(steps, torch.int32, "steps")
+            if steps.numel() != n:
+                raise ValueError("steps must hold one int32 per pose")
+        with torch.cuda.device(self.device):
+            _check(load().cddt_rm_calc_range_many(self._h, _ptr(poses), _ptr(out),
+                                                  _ptr(steps) if steps is not None else None, n,
+                                                  _stream(stream)), "cddt_rm_calc_range_many")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cddt_rm_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -308,11 +308,11 @@ def test_grid_states_and_warp_latency(G, oracle):
 
 def test_bresenham_baseline_matches_oracle(G, oracle):
     """The GPU Bresenham baseline caster walks the same digital lines as the
-    oracle's (double-precision end points, integer stepping)."""
+    oracle's (float32 end points by the direction rule, integer stepping)."""
     g = synth.rect_map(256, 256)
     d = G.CDDT(dev(g), 108, 300.0)
     q = gc.random_queries(256, 256, 20000, 31)
     q[:4] = [[-2.0, 10.0, 0.5], [10.0, 10.0, np.nan], [100.2, 50.7, 0.0], [255.4, 255.4, 0.785398]]
     got = d.cast_bresenham(dev(q)).cpu().numpy()
-    want = oracle.cast_bresenham(g, q.astype(np.float64), 300.0).astype(np.float32)
+    want = oracle.cast_bresenham(g, q, 300.0)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))

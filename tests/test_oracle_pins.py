@@ -697,3 +697,171 @@ def test_lookup_table_pins(oracle):
     got = O.lut_lookup(d.params, tab, mr, poses)
     assert got[0] == np.float32(tab[k, j, i]) / np.float32(sc) == got[1]
     assert got[2] == 0.0
+
+
+# ------------------------------------------------------------------ baselines
+
+def test_direction_rule_pins():
+    """The baseline casters' float32 cos / sin of a heading (reading D1) lie
+    within 2 ulp and 1.2e-7 of the exact values (float64 library sin and cos
+    of the same float heading; beyond 2^16 rad, of its exact remainder by the
+    float 2 pi), and the axis headings give the exact values' float
+    roundings."""
+    from oracle import oracle as O
+    rs = synth.Stream(93)
+    for lo, hi in ((-7.0, 14.0), (-65536.0, 65536.0)):
+        th = rs.uniform(40000, lo, hi).astype(np.float32)
+        s, c = O.dir_sincos(th)
+        for got, want in ((s, np.sin(th.astype(np.float64))), (c, np.cos(th.astype(np.float64)))):
+            err = np.abs(got.astype(np.float64) - want)
+            assert err.max() < 1.2e-7
+            assert np.all(err <= 2 * np.spacing(np.abs(want).astype(np.float32)))
+    th = np.array([1e5, -2.5e6, 1e7, 3e38], np.float32)
+    s, c = O.dir_sincos(th)
+    red = np.fmod(th.astype(np.float64), np.float64(np.float32(2 * np.pi)))
+    assert np.abs(s - np.sin(red)).max() < 1.2e-7 and np.abs(c - np.cos(red)).max() < 1.2e-7
+    axes = np.array([0.0, np.pi / 2, np.pi, -np.pi / 2, 2 * np.pi], np.float32)
+    s, c = O.dir_sincos(axes)
+    assert np.array_equal(s, np.sin(axes.astype(np.float64)).astype(np.float32))
+    assert np.array_equal(c, np.cos(axes.astype(np.float64)).astype(np.float32))
+
+
+def _box(W, H):
+    g = np.zeros((H, W), np.uint8)
+    g[0, :] = g[-1, :] = g[:, 0] = g[:, -1] = 1
+    return g
+
+
+def test_bresenham_closed_forms(oracle):
+    """The Bresenham caster (Section II) walks the textbook digital line: in
+    a shallow octant the cell of column x is the nearest integer to the ideal
+    line's y there.  One occupied cell on that line is hit at its centre's
+    distance; the same cell one row off the line is never met (the walk
+    leaves the map).  Axis rays in a box end at the wall cell's centre;
+    degenerate queries return 0."""
+    from oracle import oracle as O
+    rs = synth.Stream(91)
+    W, H = 80, 60
+    checked = 0
+    for trial in range(200):
+        x0, y0 = int(rs.integers(1, 2, 20)[0]), int(rs.integers(1, 2, 20)[0])
+        dx, dy = int(rs.integers(1, 20, 55)[0]), int(rs.integers(1, 0, 30)[0])
+        if dy > dx:
+            continue
+        sx = int(rs.integers(1, 0, 1)[0]) * 2 - 1  # mirror in x about the start
+        xs0 = x0 if sx > 0 else W - 1 - x0
+        th = math.atan2(dy, sx * dx)
+        R = math.hypot(dx, dy)
+        # end cell = (xs0 + sx dx, y0 + dy) exactly when R (cos, sin) lands there
+        if round(xs0 + R * math.cos(th)) != xs0 + sx * dx or round(y0 + R * math.sin(th)) != y0 + dy:
+            continue
+        k = int(rs.integers(1, 1, dx)[0])
+        num = k * dy  # y offset of column k is num / dx
+        if 2 * (num % dx) == dx:
+            continue  # a tie: either neighbour is a valid digital line
+        yk = y0 + (num + dx // 2) // dx
+        cell = (xs0 + sx * k, yk)
+        pose = np.array([[xs0, y0, th]], np.float64)
+        g = np.zeros((H, W), np.uint8)
+        g[cell[1], cell[0]] = 1
+        r = O.cast_bresenham(g, pose, R)[0]
+        assert r == np.float32(math.hypot(cell[0] - xs0, cell[1] - y0)), (trial, cell)
+        g[:] = 0
+        g[cell[1] + 1, cell[0]] = 1
+        assert O.cast_bresenham(g, pose, R)[0] == np.float32(R)
+        checked += 1
+    assert checked > 40
+    g = _box(12, 9)
+    poses = np.array([[2, 4, 0.0], [5, 2, math.pi / 2], [7, 3, math.pi], [4, 6, -math.pi / 2],
+                      [0, 4, 0.0], [-3, 4, 0.0], [3, 3, float("nan")]], np.float64)
+    r = O.cast_bresenham(g, poses, 100.0)
+    assert list(r) == [9.0, 6.0, 7.0, 6.0, 0.0, 0.0, 0.0]
+
+
+def _edt_brute(g):
+    occ = np.argwhere(g != 0)  # (row, col)
+    H, W = g.shape
+    if occ.size == 0:
+        return np.full((H, W), np.float32(W + H), np.float32)
+    jj, ii = np.mgrid[0:H, 0:W]
+    d2 = ((jj.reshape(-1, 1) - occ[None, :, 0]) ** 2 + (ii.reshape(-1, 1) - occ[None, :, 1]) ** 2).min(1)
+    return np.sqrt(d2.astype(np.float64)).astype(np.float32).reshape(H, W)
+
+
+def test_distance_transform_pins():
+    """The ray marcher's Euclidean distance transform (Section II) equals the
+    definition -- the least centre-to-centre distance to an occupied cell --
+    computed by brute force, on tiny maps of every density, a free map and a
+    fully occupied one."""
+    from oracle import oracle as O
+    maps = _tiny_maps(8, seed=23) + [np.zeros((7, 13), np.uint8), np.ones((5, 4), np.uint8), _box(12, 9)]
+    rs = synth.Stream(24)
+    for dens in (0.01, 0.2, 0.7):
+        maps.append((rs.uniform(37 * 29) < dens).astype(np.uint8).reshape(29, 37))
+    for g in maps:
+        assert np.array_equal(O.edt(g), _edt_brute(g)), g.shape
+
+
+def test_raymarch_closed_forms():
+    """Ray marching (Section II) steps by the distance to the nearest
+    obstacle.  In a box an axis ray's steps stay on cell centres and end
+    exactly on the wall cell (the hand-traced case from (2, 4) along +x in a
+    12 x 9 box reads distances 2, 4, 3, 0: range 9, 4 reads).  With a single
+    occupied cell at (x0 + 3k, y0 + 4k) the first distance is 5k and the ray
+    at atan2(4, 3) lands on it: range 5k, 2 reads (the ray at atan2(3, 4)
+    misses it).  Degenerate queries give 0; leaving the map or reaching
+    max_range gives max_range."""
+    from oracle import oracle as O
+    g = _box(12, 9)
+    E = O.edt(g)
+    r, s = O.raymarch(E, np.array([[2, 4, 0.0]], np.float32), 100.0)
+    assert r[0] == 9.0 and s[0] == 4
+    poses = np.array([[5, 2, np.pi / 2], [7, 3, np.pi], [4, 6, -np.pi / 2], [1, 1, 0.0]], np.float32)
+    r, _ = O.raymarch(E, poses, 100.0)
+    assert list(r) == [6.0, 7.0, 6.0, 10.0]
+    for k in (1, 3, 7):
+        g = np.zeros((60, 50), np.uint8)
+        x0, y0 = 4, 5
+        g[y0 + 4 * k, x0 + 3 * k] = 1
+        E = O.edt(g)
+        r, s = O.raymarch(E, np.array([[x0, y0, math.atan2(4, 3)]], np.float32), 500.0)
+        assert r[0] == np.float32(5 * k) and s[0] == 2, (k, r, s)
+        r, _ = O.raymarch(E, np.array([[x0, y0, math.atan2(3, 4)]], np.float32), 500.0)
+        assert r[0] == 500.0
+    g = _box(12, 9)
+    E = O.edt(g)
+    poses = np.array([[0, 4, 0.0], [-3, 4, 0.0], [3, 3, np.nan], [np.inf, 3, 0.0], [2, 4, 0.0]], np.float32)
+    r, s = O.raymarch(E, poses, 5.0)
+    assert list(r) == [0.0, 0.0, 0.0, 0.0, 5.0] and list(s[:4]) == [1, 0, 0, 0]
+    E = O.edt(np.zeros((9, 12), np.uint8))
+    r, _ = O.raymarch(E, np.array([[2, 4, 0.0]], np.float32), 1000.0)
+    assert r[0] == 1000.0
+
+
+def test_raymarch_against_exact_caster(oracle):
+    """A marched ray stops only on a sample inside an occupied cell, so its
+    range is never short of the exact cast's entry into the first occupied
+    cell on the ray; it matches that entry to within a cell for nearly every
+    ray (a ray that grazes a corner can step past it, the method's own
+    error)."""
+    from oracle import oracle as O
+    g = synth.rect_map(128, 128, n_rects=25, seed=61)
+    mr = 500.0
+    E = O.edt(g)
+    q = synth.uniform_queries(g, 4000, seed=64)
+    r, s = O.raymarch(E, q, mr)
+    ex = oracle.cast_exact(g, q.astype(np.float64), mr, 1)
+    assert np.all(r.astype(np.float64) >= ex - 1e-3)
+    assert np.mean(r - ex < 1.5) > 0.97
+    assert s.min() >= 1
+    occ = g != 0
+    hit = r < mr
+    px = q[hit, 0] + r[hit].astype(np.float64) * np.cos(q[hit, 2].astype(np.float64))
+    py = q[hit, 1] + r[hit].astype(np.float64) * np.sin(q[hit, 2].astype(np.float64))
+    ok = np.zeros(px.size, bool)
+    for ex_ in (-1e-3, 0.0, 1e-3):
+        for ey_ in (-1e-3, 0.0, 1e-3):
+            ix = np.floor(px + ex_ + 0.5).astype(np.int64).clip(0, g.shape[1] - 1)
+            iy = np.floor(py + ey_ + 0.5).astype(np.int64).clip(0, g.shape[0] - 1)
+            ok |= occ[iy, ix]
+    assert ok.all()
