@@ -52,7 +52,8 @@ typedef enum {
     CDDT_ERR_OOM = 3,     /* device allocation failed                               */
     CDDT_ERR_PRUNED = 4,  /* incremental update of a pruned CDDT (Section IV-D)     */
     CDDT_ERR_TIMEOUT = 5, /* a bounded device-side wait gave up                     */
-    CDDT_ERR_DEVICE = 6   /* a kernel flagged bad input; see cddt_get_status        */
+    CDDT_ERR_DEVICE = 6,  /* a kernel flagged bad input; see cddt_get_status        */
+    CDDT_ERR_BOUNDS = 7   /* (CDDT_CHECKED builds) a gather failed its bounds check  */
 } cddt_status;
 
 /* Build flags. */
@@ -468,6 +469,15 @@ CDDT_API const char *cddt_status_string(cddt_status s);
 
 /* Library version, for checks that the right build is loaded. */
 CDDT_API int32_t cddt_version(void);
+/* 1 in a bounds-checked build (compiled with -DCDDT_CHECKED=1), else 0.  In
+ * such a build every gather of the query, sensor-model, lookup-table build
+ * and prune kernels from the slice table, the bin headers and the store is
+ * checked against its buffer; one outside records CDDT_ERR_BOUNDS in the
+ * handle's device status word (read and cleared by cddt_get_status) and
+ * reads a zeroed dummy instead, so no kernel touches memory it does not own.
+ * Results of a call that tripped a check are not valid.  Slower; for
+ * testing. */
+CDDT_API int32_t cddt_checked_build(void);
 
 #ifdef __cplusplus
 }

@@ -15,6 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcddt.so")
+# the bounds-checked variant (-DCDDT_CHECKED=1): every gather of the query,
+# sensor and prune kernels is checked against its buffer
+CHECKED_DIR = os.path.join(OUT_DIR, "checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libcddt.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,11 +41,18 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "cddt.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
+
+
+def build_checked(force: bool = False) -> str:
+    """Build the bounds-checked variant of libcddt.so (a debug build)."""
+    if not force and up_to_date(CHECKED_LIB):
+        return CHECKED_LIB
+    return build(force=True, out_dir=CHECKED_DIR, defines=("CDDT_CHECKED=1",))
 
 
 def build(force: bool = False, verbose: bool = False, out_dir: str | None = None,

@@ -32,7 +32,7 @@ EXPORTED = (
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
     "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
     "cddt_lut_build", "cddt_lut_destroy", "cddt_lut_info", "cddt_lut_calc_range_many", "cddt_lut_sensor_weights",
-    "cddt_cast_bresenham", "cddt_rm_build", "cddt_rm_destroy", "cddt_rm_distances", "cddt_rm_calc_range_many",
+    "cddt_cast_bresenham", "cddt_checked_build", "cddt_rm_build", "cddt_rm_destroy", "cddt_rm_distances", "cddt_rm_calc_range_many",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -79,14 +79,16 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load libcddt.so (building it first if it is missing or stale)."""
+    """Load libcddt.so (building it first if it is missing or stale); with
+    CDDT_CHECKED=1 in the environment, its bounds-checked variant."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_missing and not _build.up_to_date():
-            _build.build()
+        checked = os.environ.get("CDDT_CHECKED", "") == "1"
+        path = _build.CHECKED_LIB if checked else _build.LIB
+        if build_if_missing and not _build.up_to_date(path):
+            _build.build_checked() if checked else _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"libcddt.so is not built ({path}); run paper_1705_01167_gb300.build")
         L = C.CDLL(path)
@@ -122,6 +124,7 @@ def load(build_if_missing: bool = True):
             "cddt_lut_build": (st, [vp, vp, C.POINTER(vp)]),
             "cddt_cast_bresenham": (st, [vp, vp, vp, i64, vp]),
             "cddt_rm_build": (st, [vp, vp, C.POINTER(vp)]),
+            "cddt_checked_build": (i32, []),
             "cddt_rm_destroy": (st, [vp]),
             "cddt_rm_distances": (st, [vp, C.POINTER(vp), C.POINTER(i64)]),
             "cddt_rm_calc_range_many": (st, [vp, vp, vp, vp, i64, vp]),

@@ -65,6 +65,8 @@ extern "C" {
 
 int32_t cddt_version(void) { return 1; }
 
+int32_t cddt_checked_build(void) { return CDDT_CHECKED; }
+
 const char *cddt_status_string(cddt_status s)
 {
     switch (s) {
@@ -75,6 +77,7 @@ const char *cddt_status_string(cddt_status s)
     case CDDT_ERR_PRUNED: return "incremental update of a pruned CDDT";
     case CDDT_ERR_TIMEOUT: return "a bounded device wait gave up";
     case CDDT_ERR_DEVICE: return "a kernel flagged bad input";
+    case CDDT_ERR_BOUNDS: return "a gather failed its bounds check (checked build)";
     }
     return "unknown status";
 }

@@ -30,6 +30,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
+#include <cstring>
+
 #include "../../include/cddt.h"
 
 namespace cddt {
@@ -59,6 +62,12 @@ struct __align__(32) BinHdr {
 constexpr uint32_t kMaxBinKeys = (1u << 24) - 1;
 __host__ __device__ __forceinline__ uint32_t bin_count(uint32_t nm) { return nm & 0xffffffu; }
 
+// A CDDT_CHECKED build checks every gather from the slice table, the bin
+// headers and the store against its buffer (chk below).
+#ifndef CDDT_CHECKED
+#define CDDT_CHECKED 0
+#endif
+
 struct MapView {
     const SliceInfo *slices;
     const BinHdr *hdr;
@@ -70,7 +79,65 @@ struct MapView {
     float Q, invQ;   // 16-bit scale and its inverse (powers of two)
     int32_t u16;
     int32_t search;  // CDDT_SEARCH_*
+#if CDDT_CHECKED
+    int64_t hdr_bytes, store_bytes;  // extents of hdr and store
+    int *status;                     // the handle's device status word
+#endif
 };
+
+#if CDDT_CHECKED
+static __device__ __align__(32) uint32_t chk_dummy[8];
+#endif
+
+// Bounds check of a gather (CDDT_CHECKED builds; elsewhere it returns p): an
+// access of `bytes` at p outside [base, base + extent) records
+// CDDT_ERR_BOUNDS in the handle's status word and reads a zeroed 32-byte
+// dummy instead, so the kernel runs to its end without touching memory it
+// does not own, and the host learns of it from cddt_get_status.
+template <typename T>
+__device__ __forceinline__ const T *chk(const MapView &m, const T *p, int bytes, const void *base, int64_t extent)
+{
+#if CDDT_CHECKED
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p), b = reinterpret_cast<uintptr_t>(base);
+    if (a < b || a + (uintptr_t)bytes > b + (uintptr_t)extent) {
+        atomicCAS(m.status, 0, (int)CDDT_ERR_BOUNDS);
+        return reinterpret_cast<const T *>(chk_dummy);
+    }
+#else
+    (void)m; (void)bytes; (void)base; (void)extent;
+#endif
+    return p;
+}
+template <typename T>
+__device__ __forceinline__ const T *chk_store(const MapView &m, const T *p, int bytes)
+{
+#if CDDT_CHECKED
+    return chk(m, p, bytes, m.store, m.store_bytes);
+#else
+    (void)m; (void)bytes;
+    return p;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ const T *chk_hdr(const MapView &m, const T *p, int bytes)
+{
+#if CDDT_CHECKED
+    return chk(m, p, bytes, m.hdr, m.hdr_bytes);
+#else
+    (void)m; (void)bytes;
+    return p;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ const T *chk_slice(const MapView &m, const T *p, int bytes)
+{
+#if CDDT_CHECKED
+    return chk(m, p, bytes, m.slices, (int64_t)m.S * (int64_t)sizeof(SliceInfo));
+#else
+    (void)m; (void)bytes;
+    return p;
+#endif
+}
 
 // ------------------------------------------------------------ geometry
 
@@ -301,8 +368,9 @@ __device__ __forceinline__ float bin_key(const MapView &m, uint32_t off, uint32_
 {
     constexpr int LK = KeyT<KT>::LK;
     const size_t leaf = (size_t)off + internal_nodes(n, LK, KeyT<KT>::R);
-    if (sizeof(KT) == 4) return __ldg(reinterpret_cast<const float *>(m.store) + (leaf << 3) + i);
-    return dequantise(__ldg(reinterpret_cast<const uint16_t *>(m.store) + (leaf << 4) + i), X, m.invQ);
+    if (sizeof(KT) == 4) return __ldg(chk_store(m, reinterpret_cast<const float *>(m.store) + (leaf << 3) + i, 4));
+    return dequantise(__ldg(chk_store(m, reinterpret_cast<const uint16_t *>(m.store) + (leaf << 4) + i, 2)), X,
+                      m.invQ);
 }
 
 // Search result: index of the first key > x (Upper) or >= x (!Upper) in the
@@ -432,11 +500,15 @@ __device__ __forceinline__ int count_below(const uint32_t (&w)[8], int from, con
 }
 
 // Key at element index e of an array of KT (scalar load, usually an L1 hit).
-template <typename KT>
+template <typename KT, bool InHdr = false>
 __device__ __forceinline__ float load_key(const MapView &m, const void *base, int64_t e, float X)
 {
-    if (sizeof(KT) == 4) return __ldg(reinterpret_cast<const float *>(base) + e);
-    return dequantise(__ldg(reinterpret_cast<const uint16_t *>(base) + e), X, m.invQ);
+    if (sizeof(KT) == 4) {
+        const float *p = reinterpret_cast<const float *>(base) + e;
+        return __ldg(InHdr ? chk_hdr(m, p, 4) : chk_store(m, p, 4));
+    }
+    const uint16_t *p = reinterpret_cast<const uint16_t *>(base) + e;
+    return dequantise(__ldg(InHdr ? chk_hdr(m, p, 2) : chk_store(m, p, 2)), X, m.invQ);
 }
 
 // Search one bin through its header and tree (layout above): count the keys
@@ -455,7 +527,7 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     r.at = kInf;
     r.prev = -kInf;
     uint32_t w[8];
-    ld_node(m.hdr + g, pol, w);
+    ld_node(chk_hdr(m, m.hdr + g, 32), pol, w);
     const uint32_t off = w[0], n = bin_count(w[1]);
     kb = (int)n;
     if (n == 0) return r;
@@ -468,8 +540,8 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
         // answer inside the bin regardless
         r.idx = min(c, (int)n);
         const void *keys = reinterpret_cast<const uint32_t *>(m.hdr + g) + 2;
-        if (r.idx < (int)n) r.at = load_key<KT>(m, keys, r.idx, X);
-        if (r.idx > 0) r.prev = load_key<KT>(m, keys, r.idx - 1, X);
+        if (r.idx < (int)n) r.at = load_key<KT, true>(m, keys, r.idx, X);
+        if (r.idx > 0) r.prev = load_key<KT, true>(m, keys, r.idx - 1, X);
         return r;
     }
     const uint32_t L0 = ((n - 1) >> LK) + 1;
@@ -484,7 +556,7 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     uint32_t loff = 0, k = (uint32_t)c;
     uint32_t cnt = (uint32_t)cnt_h;  // nodes at the current level
     for (int l = h; l >= 1; --l) {
-        ld_node(run + ((size_t)(loff + k) << 5), pol, w);
+        ld_node(chk_store(m, run + ((size_t)(loff + k) << 5), 32), pol, w);
         int cc;
         if constexpr (sizeof(KT) == 4) cc = count_below7<Upper>(w, cmp);
         else cc = count_below<KT, Upper>(w, 0, cmp);
@@ -497,7 +569,7 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     }
     // leaf (loff is now the number of internal nodes)
     const char *leaf = run + ((size_t)(loff + k) << 5);
-    ld_node(leaf, w);
+    ld_node(chk_store(m, leaf, 32), w);
     if constexpr (sizeof(KT) == 4) {
         uint32_t at, prev;
         bool prev_here;
@@ -524,7 +596,7 @@ __device__ __forceinline__ SearchResult binary_search(const MapView &m, uint32_t
     r.idx = 0;
     r.at = kInf;
     r.prev = -kInf;
-    const uint2 on = __ldg(reinterpret_cast<const uint2 *>(m.hdr + g));
+    const uint2 on = __ldg(chk_hdr(m, reinterpret_cast<const uint2 *>(m.hdr + g), 8));
     const uint32_t off = on.x;
     const int n = (int)bin_count(on.y);
     kb = n;
@@ -574,7 +646,7 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     const bool bwd = k >= S;
     const int s = bwd ? k - S : k;
     k_is_fwd = !bwd;
-    const float4 sa = __ldg(reinterpret_cast<const float4 *>(m.slices + s));
+    const float4 sa = __ldg(chk_slice(m, reinterpret_cast<const float4 *>(m.slices + s), 16));
     const float c = sa.x, sn = sa.y;
     const uint32_t Tnb = __float_as_uint(sa.w);
     const int T = (int)(Tnb & 0xffffu), nb = (int)(Tnb >> 16);
@@ -587,7 +659,7 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     f.kb = r.kb = -1;
     if (b >= 0 && b < nb) {
         const uint32_t g = __float_as_uint(sa.z) + (uint32_t)b;
-        const float X = sizeof(KT) == 4 ? 0.0f : __ldg(&m.slices[s].X);
+        const float X = sizeof(KT) == 4 ? 0.0f : __ldg(chk_slice(m, &m.slices[s].X, 4));
         int kb;
         if (!bwd || pair) {
             // forward: first key > x' (upper bound)
@@ -601,7 +673,7 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
                 float pv = sr.prev;
                 int j = sr.idx - 1;
                 if (j >= 0 && pv == xr) {
-                    const uint2 on = __ldg(reinterpret_cast<const uint2 *>(m.hdr + g));
+                    const uint2 on = __ldg(chk_hdr(m, reinterpret_cast<const uint2 *>(m.hdr + g), 8));
                     while (j >= 0 && pv == xr) {
                         --j;
                         if (j >= 0) pv = bin_key<KT>(m, on.x, bin_count(on.y), j, X);
@@ -822,6 +894,14 @@ struct cddt_s {
         v.invQ = invQ;
         v.u16 = u16;
         v.search = search;
+#if CDDT_CHECKED
+        v.hdr_bytes = (int64_t)sizeof(cddt::BinHdr) * total_bins;
+        // CDDT_FAULT=bounds: report half the store in use, so that the checks
+        // fire on valid reads (the reads themselves stay inside the buffer)
+        const char *f = std::getenv("CDDT_FAULT");
+        v.store_bytes = 32 * ((f && !std::strcmp(f, "bounds")) ? store_nodes / 2 : store_cap);
+        v.status = status;
+#endif
         return v;
     }
 };

@@ -44,7 +44,7 @@ __device__ __forceinline__ uint32_t raw_key(const KT *leaves, int i)
 }
 
 template <typename KT>
-__global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep)
+__global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t keep_n)
 {
     constexpr int LK = KeyT<KT>::LK;
     const uint64_t pol = policy_evict_last();
@@ -56,7 +56,7 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep)
         const int64_t q = t - (int64_t)s * cells;
         if (__ldg(m.grid + q)) continue;
         const int j = (int)(q / m.W), i = (int)(q - (int64_t)j * m.W);
-        const SliceInfo si = m.slices[s];
+        const SliceInfo si = *chk_slice(m, m.slices + s, (int)sizeof(SliceInfo));
         float xr, yr;
         project((float)i, (float)j, si.c, si.s, xr, yr);
         const float h = half_extent(si.c, si.s);
@@ -73,7 +73,7 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep)
         const float xlo = __fsub_rn(__fsub_rn(xr, h), eps), xhi = __fadd_rn(__fadd_rn(xr, h), eps);
         for (int b = b0; b <= b1; ++b) {
             const uint32_t g = si.sbase + (uint32_t)b;
-            const BinHdr bh = m.hdr[g];
+            const BinHdr bh = *chk_hdr(m, m.hdr + g, (int)sizeof(BinHdr));
             const uint32_t bn = bin_count(bh.nm);
             if (bn == 0) continue;
             int kb;
@@ -84,14 +84,21 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep)
             const KT *leaves = leaf_run<KT>(const_cast<void *>(m.store), bh.off, bn);
             const Cmp<KT, true> above(m, xhi, si.X);
             int u = l;
-            if (u < (int)bn && above.le(raw_key<KT>(leaves, u))) {
+            if (u < (int)bn && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) {
                 ++u;
-                while (u < (int)bn && u < l + 8 && above.le(raw_key<KT>(leaves, u))) ++u;
+                while (u < (int)bn && u < l + 8 && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0)))
+                    ++u;
                 if (u == l + 8) u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, si.X, pol, kb).idx;
             }
             const int m0 = max(l - 1, 0), m1 = min(u, (int)bn - 1);
-            uint8_t *kp = keep + (((size_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK);
-            for (int mm = m0; mm <= m1; ++mm) kp[mm] = 1;
+            const int64_t k0 = ((int64_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK;
+#if CDDT_CHECKED
+            if (m0 <= m1 && (k0 + m0 < 0 || k0 + m1 >= keep_n)) {
+                atomicCAS(m.status, 0, (int)CDDT_ERR_BOUNDS);
+                continue;
+            }
+#endif
+            for (int mm = m0; mm <= m1; ++mm) keep[k0 + mm] = 1;
         }
     }
 }
@@ -153,7 +160,8 @@ static cddt_status prune_kt(cddt_s *h, cudaStream_t st)
     CDDT_CUDA(cudaMemsetAsync(keep.p, 0, (size_t)h->store_nodes * K, st));
     const int64_t work = (int64_t)h->W * h->H * h->S;
     prune_mark_kernel<KT><<<grid_cap(work, 256, 152 * 32), 256, 0, st>>>(h->view(), prune_eps(h->W, h->H),
-                                                                          keep.as<uint8_t>());
+                                                                          keep.as<uint8_t>(),
+                                                                          h->store_nodes * K);
     count_kept_kernel<KT><<<grid_cap(nb * 32, 256), 256, 0, st>>>(h->hdr, nb, keep.as<uint8_t>(), cnt.as<uint32_t>());
     CDDT_CUDA(cudaMemcpyAsync(old_hdr.p, h->hdr, sizeof(BinHdr) * nb, cudaMemcpyDeviceToDevice, st));
     CDDT_CUDA(cudaGetLastError());

@@ -231,7 +231,7 @@ struct HotFilter {
     BeamConsts bc;
     int32_t B, D;
 };
-constexpr int kHotMax = 220;  // filters per batched launch
+constexpr int kHotMax = CDDT_CHECKED ? 180 : 220;  // filters per batched launch (parameter space)
 struct HotTable {
     HotFilter f[kHotMax];
 };

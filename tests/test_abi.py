@@ -90,3 +90,20 @@ def test_host_fault_injection(lib, monkeypatch):
     # argument errors still come first
     monkeypatch.setenv("CDDT_FAULT", "oom")
     assert lib.cddt_build(fake, 0, 10, 8, 10.0, 0, None, C.byref(h)) == cddt.CDDT_ERR_ARG
+
+
+def test_checked_variant_builds_and_exports():
+    """The bounds-checked variant (-DCDDT_CHECKED=1) builds, reports itself
+    and exports the same symbols as the normal library."""
+    import ctypes
+
+    from paper_1705_01167_gb300 import build
+    from paper_1705_01167_gb300 import cddt as G
+    lib = ctypes.CDLL(build.build_checked())
+    lib.cddt_checked_build.restype = ctypes.c_int32
+    assert lib.cddt_checked_build() == 1
+    for name in G.EXPORTED:
+        assert hasattr(lib, name), name
+    normal = ctypes.CDLL(build.build())
+    normal.cddt_checked_build.restype = ctypes.c_int32
+    assert normal.cddt_checked_build() == 0
