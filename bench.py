@@ -254,6 +254,20 @@ class Timer:
         return [a.elapsed_time(b) for a, b in ev]
 
 
+def host_cpu() -> dict:
+    """The timing host's CPU: logical cores and the model lscpu reports."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": os.uname().machine}
+
+
 def base_line(args, world, value, ms_step, workload, extra_config=None):
     cfg = {"workload": WORKLOAD_TEXT[workload], "name": workload, "l2": "flushed between steps (256 MB write)",
            "inputs": "resident in HBM"}
@@ -300,6 +314,7 @@ def run_reference(args):
     line.update({"impl": "reference", "n_gpus": args.gpus,
                  "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "sample": f"{sample} filter steps x 2500 particles x 61 beams per step"},
+                 "cpu_host": host_cpu(),
                  "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
     print(json.dumps(line))
     return 0
@@ -574,6 +589,7 @@ def bench_corridor(args, G, torch, dev, world, rank):
         dt1, n1 = cpu_oracle_run(o, w["parts"], bo, obs, 4, 1, mr)
         line["cpu_one_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": f"4 of {S} filter steps ({n1} ray casts)"}
+        line["cpu_host"] = host_cpu()
     plan.close()
     return line
 

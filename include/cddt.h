@@ -479,6 +479,23 @@ CDDT_API int32_t cddt_version(void);
  * testing. */
 CDDT_API int32_t cddt_checked_build(void);
 
+/* ---------------------------------------------------------------- tracing */
+
+/* Per-call device timing without a profiler: while on (cddt_trace_enable(1),
+ * or CDDT_TRACE=1 in the environment when the library first checks), every
+ * C-ABI call that takes a stream records a CUDA event on it at entry and at
+ * exit (none while the stream is being captured into a graph), which times
+ * the device work the call enqueued plus any idle gap it left.  Off by
+ * default; a call then pays one atomic load.  Errors: ARG (on not 0 or 1). */
+CDDT_API cddt_status cddt_trace_enable(int32_t on);
+/* Waits for the recorded events, then writes the summary since the last
+ * report as CSV text into buf (cap bytes, NUL-terminated, truncated when
+ * short; cap may be 0 with buf NULL) and clears it: a header line
+ * "entry,calls,total_ms,mean_ms,min_ms,max_ms" and one line per traced
+ * entry point.  *len (optional) receives the bytes the full text needs,
+ * NUL included.  Errors: ARG. */
+CDDT_API cddt_status cddt_trace_report(char *buf, int64_t cap, int64_t *len);
+
 #ifdef __cplusplus
 }
 #endif

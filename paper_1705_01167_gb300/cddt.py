@@ -32,7 +32,7 @@ EXPORTED = (
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
     "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
     "cddt_lut_build", "cddt_lut_destroy", "cddt_lut_info", "cddt_lut_calc_range_many", "cddt_lut_sensor_weights",
-    "cddt_cast_bresenham", "cddt_checked_build", "cddt_rm_build", "cddt_rm_destroy", "cddt_rm_distances", "cddt_rm_calc_range_many",
+    "cddt_cast_bresenham", "cddt_checked_build", "cddt_trace_enable", "cddt_trace_report", "cddt_rm_build", "cddt_rm_destroy", "cddt_rm_distances", "cddt_rm_calc_range_many",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
@@ -125,6 +125,8 @@ def load(build_if_missing: bool = True):
             "cddt_cast_bresenham": (st, [vp, vp, vp, i64, vp]),
             "cddt_rm_build": (st, [vp, vp, C.POINTER(vp)]),
             "cddt_checked_build": (i32, []),
+            "cddt_trace_enable": (st, [i32]),
+            "cddt_trace_report": (st, [C.c_char_p, i64, C.POINTER(i64)]),
             "cddt_rm_destroy": (st, [vp]),
             "cddt_rm_distances": (st, [vp, C.POINTER(vp), C.POINTER(i64)]),
             "cddt_rm_calc_range_many": (st, [vp, vp, vp, vp, i64, vp]),
@@ -529,6 +531,29 @@ class Lut:
             self.close()
         except Exception:
             pass
+
+
+def trace_enable(on: bool = True):
+    """``cddt_trace_enable``: time every C-ABI call with CUDA events on its
+    stream (see ``trace_report``)."""
+    _check(load().cddt_trace_enable(1 if on else 0), "cddt_trace_enable")
+
+
+def trace_report() -> list[dict]:
+    """``cddt_trace_report``: per entry point, the calls and their device
+    time in ms (total, mean, min, max) since the last report, which it clears."""
+    need = C.c_int64()
+    buf = C.create_string_buffer(1 << 16)
+    _check(load().cddt_trace_report(buf, len(buf), C.byref(need)), "cddt_trace_report")
+    if need.value > len(buf):
+        raise RuntimeError("cddt_trace_report: summary truncated")
+    lines = buf.value.decode().strip().splitlines()
+    out = []
+    for ln in lines[1:]:
+        name, calls, total, mean, lo, hi = ln.split(",")
+        out.append({"entry": name, "calls": int(calls), "total_ms": float(total), "mean_ms": float(mean),
+                    "min_ms": float(lo), "max_ms": float(hi)})
+    return out
 
 
 class RayMarch:

@@ -85,7 +85,7 @@ const char *cddt_status_string(cddt_status s)
 cddt_status cddt_build(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t theta_disc, float max_range,
                        uint32_t flags, void *stream, cddt_t *out)
 {
-    CDDT_RANGE("cddt_build");
+    CDDT_RANGE("cddt_build", stream);
     if (!out) return CDDT_ERR_ARG;
     *out = nullptr;
     if (!grid_dev || W < 1 || H < 1 || W > 32767 || H > 32767) return CDDT_ERR_ARG;
@@ -129,7 +129,7 @@ cddt_status cddt_import(const uint8_t *grid_dev, int32_t W, int32_t H, int32_t t
                         uint32_t flags, int32_t pruned, int64_t total_bins, const int64_t *bin_start_host,
                         const float *zp_host, void *stream, cddt_t *out)
 {
-    CDDT_RANGE("cddt_import");
+    CDDT_RANGE("cddt_import", stream);
     if (!out) return CDDT_ERR_ARG;
     *out = nullptr;
     if (!grid_dev || W < 1 || H < 1 || W > 32767 || H > 32767) return CDDT_ERR_ARG;
@@ -182,7 +182,7 @@ cddt_status cddt_destroy(cddt_t h)
 
 cddt_status cddt_prune(cddt_t h, void *stream)
 {
-    CDDT_RANGE("cddt_prune");
+    CDDT_RANGE("cddt_prune", stream);
     cddt_status rc = check_handle(h);
     if (rc != CDDT_OK) return rc;
     if (h->pruned) return CDDT_ERR_PRUNED;
@@ -192,7 +192,7 @@ cddt_status cddt_prune(cddt_t h, void *stream)
 
 cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const uint8_t *occ_dev, int32_t n, void *stream)
 {
-    CDDT_RANGE("cddt_update_cells");
+    CDDT_RANGE("cddt_update_cells", stream);
     cddt_status rc = check_handle(h);
     if (rc != CDDT_OK) return rc;
     if (n < 0 || (n > 0 && (!xy_dev || !occ_dev))) return CDDT_ERR_ARG;
@@ -205,7 +205,7 @@ cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const uint8_t *oc
 cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_dev, int64_t n, int32_t sort_by_slice,
                                  void *stream)
 {
-    CDDT_RANGE("cddt_calc_range_many");
+    CDDT_RANGE("cddt_calc_range_many", stream);
     cddt_status rc = check_handle(h);
     if (rc != CDDT_OK) return rc;
     if (n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
@@ -216,7 +216,7 @@ cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_d
 cddt_status cddt_calc_range_timed(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
                                   int64_t *warp_cycles_dev, void *stream)
 {
-    CDDT_RANGE("cddt_calc_range_timed");
+    CDDT_RANGE("cddt_calc_range_timed", stream);
     cddt_status rc = check_handle(h);
     if (rc != CDDT_OK) return rc;
     if (n < 0 || (n > 0 && (!pose_dev || !range_dev || !warp_cycles_dev))) return CDDT_ERR_ARG;
@@ -229,7 +229,7 @@ cddt_status cddt_sensor_weights(cddt_t h, const float *particles_dev, int64_t P,
                                 const float *obs_dev, int32_t B, int32_t pair_offset, const cddt_beam_model *m,
                                 float *logw_dev, float *ranges_dev, void *stream)
 {
-    CDDT_RANGE("cddt_sensor_weights");
+    CDDT_RANGE("cddt_sensor_weights", stream);
     cddt_status rc = sensor_common(h, particles_dev, P, beam_off_dev, obs_dev, B, pair_offset, m);
     if (rc != CDDT_OK) return rc;
     if (P > 0 && !logw_dev) return CDDT_ERR_ARG;
@@ -253,7 +253,7 @@ cddt_status cddt_sensor_weights_backward(cddt_t h, const float *particles_dev, i
                                          const cddt_beam_model *m, const float *grad_logw_dev, float *grad_xy_dev,
                                          void *stream)
 {
-    CDDT_RANGE("cddt_sensor_weights_backward");
+    CDDT_RANGE("cddt_sensor_weights_backward", stream);
     cddt_status rc = sensor_common(h, particles_dev, P, beam_off_dev, obs_dev, B, pair_offset, m);
     if (rc != CDDT_OK) return rc;
     if (P > 0 && (!grad_logw_dev || !grad_xy_dev)) return CDDT_ERR_ARG;
@@ -276,7 +276,7 @@ cddt_status cddt_sensor_weights_fwd_bwd(cddt_t h, const float *particles_dev, in
                                         const float *obs_dev, int32_t B, int32_t pair_offset,
                                         const cddt_beam_model *m, float *logw_dev, float *grad_xy_dev, void *stream)
 {
-    CDDT_RANGE("cddt_sensor_weights_fwd_bwd");
+    CDDT_RANGE("cddt_sensor_weights_fwd_bwd", stream);
     cddt_status rc = sensor_common(h, particles_dev, P, beam_off_dev, obs_dev, B, pair_offset, m);
     if (rc != CDDT_OK) return rc;
     if (P > 0 && (!logw_dev || !grad_xy_dev)) return CDDT_ERR_ARG;

@@ -80,7 +80,7 @@ __global__ void bresenham_kernel(const uint8_t *grid, int W, int H, const float 
 
 extern "C" cddt_status cddt_cast_bresenham(cddt_t h, const float *pose_dev, float *range_dev, int64_t n, void *stream)
 {
-    CDDT_RANGE("cddt_cast_bresenham");
+    CDDT_RANGE("cddt_cast_bresenham", stream);
     if (!h || n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_cast_bresenham");
     if (n == 0) return CDDT_OK;

@@ -111,7 +111,7 @@ extern "C" {
 
 cddt_status cddt_lut_build(cddt_t h, void *stream, cddt_lut *out)
 {
-    CDDT_RANGE("cddt_lut_build");
+    CDDT_RANGE("cddt_lut_build", stream);
     if (!h || !out) return CDDT_ERR_ARG;
     *out = nullptr;
     int dev = 0;
@@ -169,7 +169,7 @@ cddt_status cddt_lut_info(cddt_lut L, int64_t *bytes, float *scale)
 
 cddt_status cddt_lut_calc_range_many(cddt_lut L, const float *pose_dev, float *range_dev, int64_t n, void *stream)
 {
-    CDDT_RANGE("cddt_lut_calc_range_many");
+    CDDT_RANGE("cddt_lut_calc_range_many", stream);
     if (!L || n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_lut_calc_range_many");
     if (n == 0) return CDDT_OK;
@@ -183,7 +183,7 @@ cddt_status cddt_lut_sensor_weights(cddt_lut L, const float *particles_dev, int6
                                     int32_t F, const float *beam_off_dev, const float *obs_dev, int32_t B,
                                     const cddt_beam_model *m, float *logw_dev, void *stream)
 {
-    CDDT_RANGE("cddt_lut_sensor_weights");
+    CDDT_RANGE("cddt_lut_sensor_weights", stream);
     if (!L || P < 0 || F < 1 || B < 1 || !m) return CDDT_ERR_ARG;
     if (P > 0 && (!particles_dev || !seg_start_dev || !beam_off_dev || !obs_dev || !logw_dev)) return CDDT_ERR_ARG;
     if (!(m->sigma_hit > 0) || !(m->max_range > 0) || !(m->lambda_short > 0)) return CDDT_ERR_ARG;

@@ -129,7 +129,7 @@ extern "C" {
 cddt_status cddt_motion(float *particles_dev, int64_t P, const int64_t *seg_start_dev, int32_t F,
                         const float *odom_dev, const float *noise_dev, void *stream)
 {
-    CDDT_RANGE("cddt_motion");
+    CDDT_RANGE("cddt_motion", stream);
     if (P < 0 || F < 1 || (P > 0 && (!particles_dev || !seg_start_dev || !odom_dev || !noise_dev)))
         return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_motion");
@@ -144,7 +144,7 @@ cddt_status cddt_resample(const float *particles_dev, const float *logw_dev, con
                           int32_t F, const float *u0_dev, float *out_dev, int32_t *index_dev, double *scratch_dev,
                           void *stream)
 {
-    CDDT_RANGE("cddt_resample");
+    CDDT_RANGE("cddt_resample", stream);
     if (F < 1 || !particles_dev || !logw_dev || !seg_start_dev || !u0_dev || !out_dev || !scratch_dev)
         return CDDT_ERR_ARG;
     if (particles_dev == out_dev) return CDDT_ERR_ARG;

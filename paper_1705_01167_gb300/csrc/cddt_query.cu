@@ -561,7 +561,7 @@ extern "C" {
 
 cddt_status cddt_plan_create(const cddt_filter *filters_host, int32_t n_filters, void *stream, cddt_plan *out)
 {
-    CDDT_RANGE("cddt_plan_create");
+    CDDT_RANGE("cddt_plan_create", stream);
     if (!filters_host || n_filters <= 0 || !out) return CDDT_ERR_ARG;
     for (int32_t f = 0; f < n_filters; ++f) {
         const cddt_filter &F = filters_host[f];
@@ -607,7 +607,7 @@ cddt_status cddt_plan_get_shape(cddt_plan p, int32_t *tpp, int32_t *ppi, int32_t
 
 cddt_status cddt_plan_run(cddt_plan p, void *stream)
 {
-    CDDT_RANGE("cddt_plan_run");
+    CDDT_RANGE("cddt_plan_run", stream);
     if (!p) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_plan_run");
     return cddt::plan_run(p, (cudaStream_t)stream);
@@ -615,7 +615,7 @@ cddt_status cddt_plan_run(cddt_plan p, void *stream)
 
 cddt_status cddt_plan_launch_graph(cddt_plan p, void *stream)
 {
-    CDDT_RANGE("cddt_plan_launch_graph");
+    CDDT_RANGE("cddt_plan_launch_graph", stream);
     if (!p) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_plan_launch_graph");
     return cddt::plan_launch_graph(p, (cudaStream_t)stream);

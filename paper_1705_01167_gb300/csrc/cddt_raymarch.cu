@@ -157,7 +157,7 @@ extern "C" {
 
 cddt_status cddt_rm_build(cddt_t h, void *stream, cddt_rm *out)
 {
-    CDDT_RANGE("cddt_rm_build");
+    CDDT_RANGE("cddt_rm_build", stream);
     if (!h || !out) return CDDT_ERR_ARG;
     *out = nullptr;
     int dev = 0;
@@ -215,7 +215,7 @@ cddt_status cddt_rm_distances(cddt_rm R, const float **dist_dev, int64_t *bytes)
 cddt_status cddt_rm_calc_range_many(cddt_rm R, const float *pose_dev, float *range_dev, int32_t *steps_dev,
                                     int64_t n, void *stream)
 {
-    CDDT_RANGE("cddt_rm_calc_range_many");
+    CDDT_RANGE("cddt_rm_calc_range_many", stream);
     if (!R || n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_rm_calc_range_many");
     if (n == 0) return CDDT_OK;

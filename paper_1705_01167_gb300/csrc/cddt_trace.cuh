@@ -1,7 +1,10 @@
 // cddt_trace.cuh -- NVTX ranges around the C-ABI calls (shown by Nsight
-// tools, no-ops without one attached) and the host-side fault injection
-// read from the CDDT_FAULT environment variable.
+// tools, no-ops without one attached), an optional CUDA-event trace of the
+// same calls (cddt_trace_enable / cddt_trace_report, or CDDT_TRACE=1), and
+// the host-side fault injection read from the CDDT_FAULT environment
+// variable.
 #pragma once
+#include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <cstdlib>
@@ -11,11 +14,32 @@
 
 namespace cddt {
 
+// Event trace (implemented in cddt_api.cu): when on, each call records a
+// CUDA event on its stream at entry and at exit (not while the stream is
+// being captured into a graph); the pairs are timed and summed per entry
+// point when the trace is reported.
+bool trace_on();
+void trace_begin(cudaStream_t st, cudaEvent_t &a);
+void trace_end(const char *name, cudaStream_t st, cudaEvent_t a);
+
 struct Range {
-    explicit Range(const char *name) { nvtxRangePushA(name); }
-    ~Range() { nvtxRangePop(); }
+    Range(const char *name, void *stream) : name_(name), st_(static_cast<cudaStream_t>(stream))
+    {
+        nvtxRangePushA(name);
+        if (trace_on()) trace_begin(st_, a_);
+    }
+    ~Range()
+    {
+        if (a_) trace_end(name_, st_, a_);
+        nvtxRangePop();
+    }
     Range(const Range &) = delete;
     Range &operator=(const Range &) = delete;
+
+  private:
+    const char *name_;
+    cudaStream_t st_;
+    cudaEvent_t a_ = nullptr;
 };
 
 // CDDT_FAULT=<kind>[:<entry point>] makes the named C-ABI entry point (every
@@ -40,7 +64,7 @@ inline cddt_status injected_fault(const char *entry)
 
 }  // namespace cddt
 
-#define CDDT_RANGE(name) cddt::Range cddt_range_(name)
+#define CDDT_RANGE(name, stream) cddt::Range cddt_range_(name, stream)
 #define CDDT_FAULT_POINT(name)                                                \
     do {                                                                      \
         cddt_status f_ = cddt::injected_fault(name);                          \

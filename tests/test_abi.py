@@ -107,3 +107,26 @@ def test_checked_variant_builds_and_exports():
     normal = ctypes.CDLL(build.build())
     normal.cddt_checked_build.restype = ctypes.c_int32
     assert normal.cddt_checked_build() == 0
+
+
+def test_trace_host_side(lib):
+    """The call trace: enable / disable, an empty report with its header, a
+    short buffer truncated with the needed length reported, and calls that
+    fail their argument checks while tracing is on still return ARG."""
+    from paper_1705_01167_gb300 import cddt
+    assert lib.cddt_trace_enable(2) == cddt.CDDT_ERR_ARG
+    assert lib.cddt_trace_enable(1) == cddt.CDDT_OK
+    try:
+        h = C.c_void_p(0)
+        assert lib.cddt_build(None, 10, 10, 8, 10.0, 0, None, C.byref(h)) == cddt.CDDT_ERR_ARG
+        need = C.c_int64()
+        assert lib.cddt_trace_report(None, 0, C.byref(need)) == cddt.CDDT_OK
+        header = b"entry,calls,total_ms,mean_ms,min_ms,max_ms\n"
+        assert need.value >= len(header) + 1
+        buf = C.create_string_buffer(8)
+        assert lib.cddt_trace_report(buf, 8, C.byref(need)) == cddt.CDDT_OK
+        assert buf.value == header[:7]
+        assert lib.cddt_trace_report(None, 5, None) == cddt.CDDT_ERR_ARG
+        assert cddt.trace_report() == []
+    finally:
+        assert lib.cddt_trace_enable(0) == cddt.CDDT_OK
