@@ -525,6 +525,21 @@ def bench_corridor(args, G, torch, dev, world, rank):
 
 
 
+    # the 16-bit zero-point store (Section IV-C's compression; reading S7):
+    # half the key bytes, ranges quantised to 1/Q of a cell
+    du = G.CDDT(grid, w["theta_disc"], mr, u16=True)
+    stu = du.stats()
+    plan_u = G.Plan(filters_for(du))
+    shape_u = plan_u.autotune()
+    ms_u = timed(plan_u.run, k2, 2)
+    ms_uu = timed(lambda: du.calc_range_many(sw, out=out), 5, 2)
+    extra["u16"] = {"rays_per_s": rays_per_step / (statistics.mean(ms_u) * 1e-3),
+                    "sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_uu) * 1e-3),
+                    "store_bytes": stu["store_bytes"], "f32_store_bytes": st0["store_bytes"],
+                    "build_ms": stu["build_ms"], "shape": shape_u}
+    plan_u.close()
+    du.close()
+
     dp = G.CDDT(grid, w["theta_disc"], mr)
     dp.prune()
     stp = dp.stats()

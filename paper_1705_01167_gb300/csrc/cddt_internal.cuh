@@ -385,8 +385,13 @@ struct SearchResult {
 // Comparison of node keys against a query abscissa.  float32 keys compare
 // directly; 16-bit keys compare as integers against the exact threshold:
 // value(key) = key / Q - X is exact in float32, so value(key) <= x iff
-// key <= floor((x + X) Q) and value(key) < x iff key <= ceil((x + X) Q) - 1,
-// evaluated in double where x + X and the product are exact.
+// key <= floor((x + X) Q) and value(key) < x iff key <= ceil((x + X) Q) - 1.
+// The threshold is exact in float32 arithmetic: x + X = s + e exactly
+// (Knuth's TwoSum), Q is a power of two, and floor(sQ + eQ) is floor(sQ)
+// unless sQ is an integer, when it is sQ + floor(eQ) (|eQ| is at most half
+// an ulp of sQ, so it cannot cross an integer otherwise); likewise for
+// ceil.  (A float64 evaluation is as slow as the search on GB300, and not
+// exact when x and X differ by more than 29 binary orders.)
 template <typename KT, bool Upper> struct Cmp;
 template <bool Upper> struct Cmp<float, Upper> {
     float x;
@@ -401,10 +406,19 @@ template <bool Upper> struct Cmp<uint16_t, Upper> {
     int t;
     __device__ __forceinline__ Cmp(const MapView &m, float x, float X)
     {
-        double xx = ((double)x + (double)X) * (double)m.Q;
-        double tt = Upper ? floor(xx) : ceil(xx) - 1.0;
-        tt = fmax(-1.0, fmin(65536.0, tt));
-        t = (int)tt;
+        const float s = __fadd_rn(x, X);
+        const float bp = __fsub_rn(s, x);
+        const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bp)), __fsub_rn(X, bp));
+        const float f = __fmul_rn(s, m.Q), eq = __fmul_rn(e, m.Q);
+        float tt;
+        if (Upper) {
+            const float fl = floorf(f);
+            tt = fl == f ? __fadd_rn(f, floorf(eq)) : fl;
+        } else {
+            const float cl = ceilf(f);
+            tt = __fsub_rn(cl == f ? __fadd_rn(f, ceilf(eq)) : cl, 1.0f);
+        }
+        t = (int)fminf(fmaxf(tt, -1.0f), 65536.0f);
     }
     __device__ __forceinline__ bool le(uint32_t key) const { return (int)key <= t; }
 };
@@ -482,6 +496,53 @@ __device__ __forceinline__ int count_below6(const uint32_t (&w)[8], const Cmp<fl
     return (b2 ? 4 : 0) + (b1 ? 2 : 0) + (b0 ? 1 : 0);
 }
 
+// 16-bit keys: key j of a node is half (j & 1) of word j >> 1; a header's
+// key i sits where node key i + 4 would.  Word and key selection by a select
+// tree (a register array indexed at run time would go to local memory).
+__device__ __forceinline__ uint32_t sel_word(const uint32_t (&w)[8], int i)
+{
+    const bool o = i & 1;
+    const uint32_t a = o ? w[1] : w[0], b = o ? w[3] : w[2], c = o ? w[5] : w[4], d = o ? w[7] : w[6];
+    const uint32_t e = (i & 2) ? b : a, f = (i & 2) ? d : c;
+    return (i & 4) ? f : e;
+}
+__device__ __forceinline__ uint32_t key16_at(const uint32_t (&w)[8], int j)
+{
+    return (sel_word(w, j >> 1) >> ((j & 1) * 16)) & 0xffffu;
+}
+
+// Number of a 16-bit node's keys below the query when it is at most 15 (a
+// node below the root: its largest key is its separator, not below the
+// query): four comparisons, each choosing the key the next one looks at.
+template <bool Upper>
+__device__ __forceinline__ int count_below15(const uint32_t (&w)[8], const Cmp<uint16_t, Upper> &cmp)
+{
+    const bool b3 = cmp.le(w[3] >> 16);                    // key 7
+    const bool b2 = cmp.le((b3 ? w[5] : w[1]) >> 16);      // key 8 b3 + 3
+    const uint32_t lo = b2 ? w[2] : w[0], hi = b2 ? w[6] : w[4];
+    const bool b1 = cmp.le((b3 ? hi : lo) >> 16);          // key 8 b3 + 4 b2 + 1
+    const int wi = (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+    const bool b0 = cmp.le(sel_word(w, wi) & 0xffffu);     // key 2 wi
+    return 2 * wi + (b0 ? 1 : 0);
+}
+
+// The same for the 12 keys of a 16-bit header (0..12 below), positions
+// 12..15 counting as above every query.
+template <bool Upper>
+__device__ __forceinline__ int count_below12(const uint32_t (&w)[8], const Cmp<uint16_t, Upper> &cmp)
+{
+    const bool b3 = cmp.le(w[5] >> 16);                    // key 7
+    const bool b2 = cmp.le((b3 ? w[7] : w[3]) >> 16);      // key 8 b3 + 3
+    const bool top = b3 && b2;                             // keys 13 and 12 do not exist
+    const bool b1 = !top && cmp.le((b3 ? w[6] : (b2 ? w[4] : w[2])) >> 16);  // key 8 b3 + 4 b2 + 1
+    const int wi = (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+    const bool o = wi & 1;
+    const uint32_t x0 = o ? w[3] : w[2], x1 = o ? w[5] : w[4], x2 = o ? w[7] : w[6];
+    const uint32_t word = (wi & 4) ? x2 : ((wi & 2) ? x1 : x0);
+    const bool b0 = !top && cmp.le(word & 0xffffu);        // key 8 b3 + 4 b2 + 2 b1
+    return 2 * wi + (b0 ? 1 : 0);
+}
+
 // Number of a node's keys below the query (keys ascending, padding above).
 template <typename KT, bool Upper>
 __device__ __forceinline__ int count_below(const uint32_t (&w)[8], int from, const Cmp<KT, Upper> &cmp)
@@ -534,14 +595,19 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     const Cmp<KT, Upper> cmp(m, x, X);
     int c;
     if constexpr (sizeof(KT) == 4) c = count_below6<Upper>(w, cmp);
-    else c = count_below<KT, Upper>(w, 2, cmp);
+    else c = count_below12<Upper>(w, cmp);
     if (n <= (uint32_t)R) {  // the keys themselves are in the header
         // padding never compares below an in-map query; the clamp keeps the
         // answer inside the bin regardless
         r.idx = min(c, (int)n);
-        const void *keys = reinterpret_cast<const uint32_t *>(m.hdr + g) + 2;
-        if (r.idx < (int)n) r.at = load_key<KT, true>(m, keys, r.idx, X);
-        if (r.idx > 0) r.prev = load_key<KT, true>(m, keys, r.idx - 1, X);
+        if constexpr (sizeof(KT) == 4) {
+            const void *keys = reinterpret_cast<const uint32_t *>(m.hdr + g) + 2;
+            if (r.idx < (int)n) r.at = load_key<KT, true>(m, keys, r.idx, X);
+            if (r.idx > 0) r.prev = load_key<KT, true>(m, keys, r.idx - 1, X);
+        } else {  // from the header's registers
+            if (r.idx < (int)n) r.at = dequantise(key16_at(w, r.idx + 4), X, m.invQ);
+            if (r.idx > 0) r.prev = dequantise(key16_at(w, r.idx + 3), X, m.invQ);
+        }
         return r;
     }
     const uint32_t L0 = ((n - 1) >> LK) + 1;
@@ -559,7 +625,7 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
         ld_node(chk_store(m, run + ((size_t)(loff + k) << 5), 32), pol, w);
         int cc;
         if constexpr (sizeof(KT) == 4) cc = count_below7<Upper>(w, cmp);
-        else cc = count_below<KT, Upper>(w, 0, cmp);
+        else cc = count_below15<Upper>(w, cmp);
         loff += cnt;
         cnt = ((L0 - 1) >> (LK * (l - 1))) + 1;  // nodes one level down
         k = k * K + (uint32_t)cc;
@@ -579,11 +645,14 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
         if (prev_here) r.prev = __uint_as_float(prev);
         else if (k > 0) r.prev = load_key<KT>(m, leaf, -1, X);
     } else {
-        c = count_below<KT, Upper>(w, 0, cmp);
+        // at most 15 keys of the chosen leaf are below (its largest is its
+        // separator); the answer's neighbours come from the registers
+        c = count_below15<Upper>(w, cmp);
         r.idx = min((int)(k * K) + c, (int)n);
-        const int cl = r.idx - (int)(k * K);  // index inside this leaf (may be -1 .. K)
-        if (r.idx < (int)n) r.at = load_key<KT>(m, leaf, cl, X);
-        if (r.idx > 0) r.prev = load_key<KT>(m, leaf, cl - 1, X);
+        const int cl = r.idx - (int)(k * K);  // index inside this leaf, 0 .. 15
+        if (r.idx < (int)n) r.at = dequantise(key16_at(w, cl), X, m.invQ);
+        if (cl > 0) r.prev = dequantise(key16_at(w, cl - 1), X, m.invQ);
+        else if (r.idx > 0) r.prev = load_key<KT>(m, leaf, -1, X);
     }
     return r;
 }
