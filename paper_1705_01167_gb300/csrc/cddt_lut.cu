@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <vector>
 
 #include "cddt_internal.cuh"
 #include "cddt_kernels.cuh"
@@ -29,9 +30,10 @@ __device__ __forceinline__ uint16_t lut_code(float r, float scale)
 }
 
 // Every state of one theta_k per block row: the cast from the cell centre
-// (i, j) in direction 2 pi k / N (computed in double, stored float32).
+// (i, j) in direction theta[k] = 2 pi k / N (computed in double on the host,
+// stored float32).
 template <typename KT, int SEARCH>
-__global__ void lut_build_kernel(MapView m, uint16_t *table, float scale)
+__global__ void lut_build_kernel(MapView m, const float *theta, uint16_t *table, float scale)
 {
     const uint64_t pol = policy_evict_last();
     const int64_t cells = (int64_t)m.W * m.H;
@@ -41,7 +43,7 @@ __global__ void lut_build_kernel(MapView m, uint16_t *table, float scale)
         const int k = (int)(t / cells);
         const int64_t q = t - (int64_t)k * cells;
         const int j = (int)(q / m.W), i = (int)(q - (int64_t)j * m.W);
-        const float th = (float)((2.0 * 3.14159265358979323846 * (double)k) / (double)m.N);
+        const float th = __ldg(theta + k);
         Cast c;
         c.r = 0.0f;
         if (free_cell(m.grid, m.W, m.H, (float)i, (float)j)) {
@@ -133,15 +135,35 @@ cddt_status cddt_lut_build(cddt_t h, void *stream, cddt_lut *out)
         delete L;
         return CDDT_ERR_OOM;
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    // the N table directions, one float each (the kernel reads them instead
+    // of evaluating the double expression per state)
+    std::vector<float> th_h((size_t)h->N);
+    for (int k = 0; k < h->N; ++k) th_h[k] = (float)((2.0 * 3.14159265358979323846 * (double)k) / (double)h->N);
+    float *th = nullptr;
+    if (cudaMallocAsync(&th, sizeof(float) * th_h.size(), st) != cudaSuccess) {
+        cudaFree(L->table);
+        delete L;
+        return CDDT_ERR_OOM;
+    }
+    // the pageable source is consumed before the call returns
+    cudaError_t ce = cudaMemcpyAsync(th, th_h.data(), sizeof(float) * th_h.size(), cudaMemcpyHostToDevice, st);
     const cddt::MapView m = h->view();
     const unsigned blocks = cddt::grid_cap(n, 256, 152 * 64);
-    cudaStream_t st = (cudaStream_t)stream;
     const bool bin = h->search == CDDT_SEARCH_BINARY;
-    if (h->u16 && bin) cddt::lut_build_kernel<uint16_t, CDDT_SEARCH_BINARY><<<blocks, 256, 0, st>>>(m, L->table, L->scale);
-    else if (h->u16) cddt::lut_build_kernel<uint16_t, CDDT_SEARCH_TREE><<<blocks, 256, 0, st>>>(m, L->table, L->scale);
-    else if (bin) cddt::lut_build_kernel<float, CDDT_SEARCH_BINARY><<<blocks, 256, 0, st>>>(m, L->table, L->scale);
-    else cddt::lut_build_kernel<float, CDDT_SEARCH_TREE><<<blocks, 256, 0, st>>>(m, L->table, L->scale);
-    if (cudaGetLastError() != cudaSuccess) {
+    if (ce == cudaSuccess) {
+        if (h->u16 && bin)
+            cddt::lut_build_kernel<uint16_t, CDDT_SEARCH_BINARY><<<blocks, 256, 0, st>>>(m, th, L->table, L->scale);
+        else if (h->u16)
+            cddt::lut_build_kernel<uint16_t, CDDT_SEARCH_TREE><<<blocks, 256, 0, st>>>(m, th, L->table, L->scale);
+        else if (bin)
+            cddt::lut_build_kernel<float, CDDT_SEARCH_BINARY><<<blocks, 256, 0, st>>>(m, th, L->table, L->scale);
+        else
+            cddt::lut_build_kernel<float, CDDT_SEARCH_TREE><<<blocks, 256, 0, st>>>(m, th, L->table, L->scale);
+        ce = cudaGetLastError();
+    }
+    cudaFreeAsync(th, st);
+    if (ce != cudaSuccess) {
         cudaFree(L->table);
         delete L;
         return CDDT_ERR_CUDA;
