@@ -526,6 +526,31 @@ __device__ __forceinline__ int count_below15(const uint32_t (&w)[8], const Cmp<u
     return 2 * wi + (b0 ? 1 : 0);
 }
 
+// The same count for a 16-bit leaf, with the keys either side of the answer
+// taken from what the search already holds: at = key[c], prev = key[c - 1]
+// (the last comparison read key 2 wi, and key 2 wi - 1 is the key of the
+// latest comparison that went the other way); prev_here is false for c = 0.
+template <bool Upper>
+__device__ __forceinline__ int leaf_count15(const uint32_t (&w)[8], const Cmp<uint16_t, Upper> &cmp, uint32_t &at,
+                                            uint32_t &prev, bool &prev_here)
+{
+    const uint32_t k7 = w[3] >> 16;
+    const bool b3 = cmp.le(k7);
+    const uint32_t k3 = (b3 ? w[5] : w[1]) >> 16;          // key 8 b3 + 3
+    const bool b2 = cmp.le(k3);
+    const uint32_t lo = b2 ? w[2] : w[0], hi = b2 ? w[6] : w[4];
+    const uint32_t k1 = (b3 ? hi : lo) >> 16;              // key 8 b3 + 4 b2 + 1
+    const bool b1 = cmp.le(k1);
+    const int wi = (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+    const uint32_t word = sel_word(w, wi);
+    const uint32_t k0 = word & 0xffffu;                    // key 2 wi
+    const bool b0 = cmp.le(k0);
+    at = b0 ? word >> 16 : k0;
+    prev = b0 ? k0 : (b1 ? k1 : (b2 ? k3 : k7));
+    prev_here = b0 || b1 || b2 || b3;
+    return 2 * wi + (b0 ? 1 : 0);
+}
+
 // The same for the 12 keys of a 16-bit header (0..12 below), positions
 // 12..15 counting as above every query.
 template <bool Upper>
@@ -647,12 +672,15 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     } else {
         // at most 15 keys of the chosen leaf are below (its largest is its
         // separator); the answer's neighbours come from the registers
-        c = count_below15<Upper>(w, cmp);
-        r.idx = min((int)(k * K) + c, (int)n);
-        const int cl = r.idx - (int)(k * K);  // index inside this leaf, 0 .. 15
-        if (r.idx < (int)n) r.at = dequantise(key16_at(w, cl), X, m.invQ);
-        if (cl > 0) r.prev = dequantise(key16_at(w, cl - 1), X, m.invQ);
-        else if (r.idx > 0) r.prev = load_key<KT>(m, leaf, -1, X);
+        uint32_t at, prev;
+        bool prev_here;
+        c = leaf_count15<Upper>(w, cmp, at, prev, prev_here);
+        const int raw = (int)(k * K) + c;
+        r.idx = min(raw, (int)n);  // padding is below only a query beyond the map
+        if (r.idx < (int)n) r.at = dequantise(at, X, m.invQ);
+        if (raw > (int)n) r.prev = load_key<KT>(m, leaf, (int64_t)n - 1 - (int64_t)(k * K), X);
+        else if (prev_here) r.prev = dequantise(prev, X, m.invQ);
+        else if (k > 0) r.prev = load_key<KT>(m, leaf, -1, X);
     }
     return r;
 }
