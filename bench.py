@@ -466,7 +466,6 @@ def bench_corridor(args, G, torch, dev, world, rank):
         lat[name] = {"p25": float(np.percentile(c, 25)), "median": float(np.median(c)),
                      "p75": float(np.percentile(c, 75)), "p99": float(np.percentile(c, 99)), "mean": float(c.mean())}
     extra["warp_latency_cycles"] = lat
-    del gq, gout
 
     # the paper's comparison: a 16-bit lookup table of every state, built on
     # the GPU from this CDDT; the same sensor model over table reads (all 200
@@ -483,7 +482,9 @@ def bench_corridor(args, G, torch, dev, world, rank):
     extra["lut"] = {"build_ms": ev0.elapsed_time(ev1), "bytes": lut.info()["bytes"],
                     "cddt_store_bytes": st0["store_bytes"],
                     "sensor_rays_per_s": rays_per_step / (statistics.mean(ms_lut) * 1e-3),
-                    "sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_lsw) * 1e-3)}
+                    "sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_lsw) * 1e-3),
+                    "grid_sweep_rays_per_s": gq.shape[0] / (statistics.mean(
+                        timed(lambda: lut.calc_range_many(gq, out=gout), 3, 1)) * 1e-3)}
     lut.close()
     del lut_out
 
@@ -497,7 +498,9 @@ def bench_corridor(args, G, torch, dev, world, rank):
     fr_out = torch.empty(fr.shape[0], dtype=torch.float32, device=dev)
     ms_blf = timed(lambda: d.cast_bresenham(fr, out=fr_out), 3, 1)
     ms_cf = timed(lambda: d.calc_range_many(fr, out=fr_out), 3, 1)
+    ms_blg = timed(lambda: d.cast_bresenham(gq, out=gout), 3, 1)
     extra["bresenham"] = {"sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_bl) * 1e-3),
+                          "grid_sweep_rays_per_s": gq.shape[0] / (statistics.mean(ms_blg) * 1e-3),
                           "filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_blf) * 1e-3),
                           "cddt_filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_cf) * 1e-3)}
 
@@ -511,10 +514,12 @@ def bench_corridor(args, G, torch, dev, world, rank):
     rm_build_ms = (time.perf_counter() - t0) * 1e3
     ms_rm = timed(lambda: rm.calc_range_many(sw, out=bl_out), 3, 1)
     ms_rmf = timed(lambda: rm.calc_range_many(fr, out=fr_out), 3, 1)
+    ms_rmg = timed(lambda: rm.calc_range_many(gq, out=gout), 3, 1)
     rm_steps = torch.empty(sw.shape[0], dtype=torch.int32, device=dev)
     rm.calc_range_many(sw, out=bl_out, steps=rm_steps)
     st_f = rm_steps.float()
     extra["raymarch"] = {"sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_rm) * 1e-3),
+                         "grid_sweep_rays_per_s": gq.shape[0] / (statistics.mean(ms_rmg) * 1e-3),
                          "filter_rays_per_s": fr.shape[0] / (statistics.mean(ms_rmf) * 1e-3),
                          "build_ms": rm_build_ms, "transform_bytes": 4 * grid.shape[0] * grid.shape[1],
                          "sweep_reads_mean": float(st_f.mean()),
@@ -533,8 +538,10 @@ def bench_corridor(args, G, torch, dev, world, rank):
     shape_u = plan_u.autotune()
     ms_u = timed(plan_u.run, k2, 2)
     ms_uu = timed(lambda: du.calc_range_many(sw, out=out), 5, 2)
+    ms_ug = timed(lambda: du.calc_range_many(gq, out=gout), 3, 1)
     extra["u16"] = {"rays_per_s": rays_per_step / (statistics.mean(ms_u) * 1e-3),
                     "sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_uu) * 1e-3),
+                    "grid_sweep_rays_per_s": gq.shape[0] / (statistics.mean(ms_ug) * 1e-3),
                     "store_bytes": stu["store_bytes"], "f32_store_bytes": st0["store_bytes"],
                     "build_ms": stu["build_ms"], "shape": shape_u}
     plan_u.close()
@@ -551,6 +558,20 @@ def bench_corridor(args, G, torch, dev, world, rank):
     extra["pruned_zero_points"] = stp["n_zero_points"]
     ms_pu = timed(lambda: dp.calc_range_many(sw, out=out), 5, 2)
     extra["pruned_sweep_rays_per_s"] = sw.shape[0] / (statistics.mean(ms_pu) * 1e-3)
+    ms_pg = timed(lambda: dp.calc_range_many(gq, out=gout), 3, 1)
+    extra["pruned_grid_sweep_rays_per_s"] = gq.shape[0] / (statistics.mean(ms_pg) * 1e-3)
+    # the paper's comparison of methods (Section V): ray casts/s on the random
+    # and the grid samples, the CDDT against its variants and the baselines
+    extra["methods"] = {
+        "cddt": {"random": extra["sweep_rays_per_s"], "grid": extra["grid_sweep_rays_per_s"]},
+        "pcddt": {"random": extra["pruned_sweep_rays_per_s"], "grid": extra["pruned_grid_sweep_rays_per_s"]},
+        "cddt_u16": {"random": extra["u16"]["sweep_rays_per_s"], "grid": extra["u16"]["grid_sweep_rays_per_s"]},
+        "lut": {"random": extra["lut"]["sweep_rays_per_s"], "grid": extra["lut"]["grid_sweep_rays_per_s"]},
+        "ray_marching": {"random": extra["raymarch"]["sweep_rays_per_s"],
+                         "grid": extra["raymarch"]["grid_sweep_rays_per_s"]},
+        "bresenham": {"random": extra["bresenham"]["sweep_rays_per_s"],
+                      "grid": extra["bresenham"]["grid_sweep_rays_per_s"]}}
+    del gq, gout
     plan_p.close()
 
     # end to end through the public API from pinned host buffers
