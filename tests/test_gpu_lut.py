@@ -63,3 +63,36 @@ def test_lut_matches_oracle(G, oracle, u16):
                                                     oracle.beam_model(mr)) for f in range(3)])
         assert (np.abs(lw - want) <= 1e-5 * np.maximum(1.0, np.abs(want))).all()
     lut.close()
+
+
+def test_lut_full_size_sampled(G, oracle):
+    """The 2000 x 2000 corridor map at theta_disc 200 (the bench's table,
+    1.6 GB): sampled states read back exactly as the oracle's coded cast of
+    that state, and continuous queries read their nearest state's entry."""
+    from oracle import oracle as O
+    g = synth.corridor_map(2000, 2000)
+    N, mr = 200, 1000.0
+    d = G.CDDT(dev(g), N, mr)
+    lut = G.Lut(d)
+    o = oracle.OracleCDDT(g, N, mr)
+    sc = np.float32(O.lut_scale(mr))
+
+    def coded(r):
+        code = np.clip(np.floor(r * sc + np.float32(0.5)), 0, 65535).astype(np.float32)
+        return (code / sc).astype(np.float32)
+
+    rs = synth.Stream(131)
+    n = 20000
+    i = rs.integers(n, 0, 1999)
+    j = rs.integers(n, 0, 1999)
+    k = rs.integers(n, 0, N - 1)
+    th = np.array([np.float32(2.0 * np.pi * kk / N) for kk in k], np.float32)
+    st = np.stack([i, j, th], 1).astype(np.float32)
+    got = lut.calc_range_many(dev(st)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), coded(o.calc_range(st)).view(np.uint32))
+    q = synth.uniform_queries(g, 20000, seed=132)
+    ks = np.array([o.params.query_k(float(t)) for t in q[:, 2]])
+    snap = np.stack([np.floor(q[:, 0] + np.float32(0.5)), np.floor(q[:, 1] + np.float32(0.5)),
+                     np.array([np.float32(2.0 * np.pi * kk / N) for kk in ks], np.float32)], 1).astype(np.float32)
+    got = lut.calc_range_many(dev(q)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), coded(o.calc_range(snap)).view(np.uint32))

@@ -316,3 +316,15 @@ def test_bresenham_baseline_matches_oracle(G, oracle):
     got = d.cast_bresenham(dev(q)).cpu().numpy()
     want = oracle.cast_bresenham(g, q, 300.0)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_bresenham_full_size(G, oracle):
+    """The Bresenham baseline on the bench's 2000 x 2000 corridor map (max
+    range 1000): uniform queries and edge cases walked one by one by the
+    oracle."""
+    g = synth.corridor_map(2000, 2000)
+    d = G.CDDT(dev(g), 200, 1000.0)
+    q = np.concatenate([gc.special_queries(2000, 2000), synth.uniform_queries(g, 30000, seed=33)])
+    got = d.cast_bresenham(dev(q)).cpu().numpy()
+    want = oracle.cast_bresenham(g, q, 1000.0)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
