@@ -716,7 +716,8 @@ def test_direction_rule_pins():
             err = np.abs(got.astype(np.float64) - want)
             assert err.max() < 1.2e-7
             assert np.all(err <= 2 * np.spacing(np.abs(want).astype(np.float32)))
-    th = np.array([1e5, -2.5e6, 1e7, 3e38], np.float32)
+    th = np.concatenate([np.array([1e5, -2.5e6, 1e7, 3e38], np.float32),
+                         rs.uniform(40, 7e4, 1e8).astype(np.float32)])
     s, c = O.dir_sincos(th)
     red = np.fmod(th.astype(np.float64), np.float64(np.float32(2 * np.pi)))
     assert np.abs(s - np.sin(red)).max() < 1.2e-7 and np.abs(c - np.cos(red)).max() < 1.2e-7
@@ -776,6 +777,24 @@ def test_bresenham_closed_forms(oracle):
                       [0, 4, 0.0], [-3, 4, 0.0], [3, 3, float("nan")]], np.float64)
     r = O.cast_bresenham(g, poses, 100.0)
     assert list(r) == [9.0, 6.0, 7.0, 6.0, 0.0, 0.0, 0.0]
+    # the start cell is the nearest cell centre: (0.6, 4.2) starts in the free
+    # cell (1, 4), not the wall cell (0, 4), and meets the wall at (11, 4)
+    r = O.cast_bresenham(g, np.array([[0.6, 4.2, 0.0]], np.float32), 100.0)[0]
+    dx, dy = np.float32(11) - np.float32(0.6), np.float32(4) - np.float32(4.2)
+    assert r == np.sqrt(dx * dx + dy * dy)
+    # a tie of the error term, traced by hand through the textbook all-octant
+    # stepping (err = dx - |dy|; step x when 2 err >= -|dy|, y when 2 err <=
+    # dx): (5, 5) -> (9, 7) visits (6, 6), (7, 6), (8, 7), (9, 7)
+    R = math.hypot(4, 2)
+    pose = np.array([[5, 5, math.atan2(2, 4)]], np.float32)
+    for cell, want in (((6, 6), math.sqrt(2)), ((7, 6), math.sqrt(5)), ((8, 7), math.sqrt(13))):
+        g = np.zeros((12, 12), np.uint8)
+        g[cell[1], cell[0]] = 1
+        assert O.cast_bresenham(g, pose, R)[0] == np.float32(want), cell
+    for cell in ((6, 5), (7, 7)):
+        g = np.zeros((12, 12), np.uint8)
+        g[cell[1], cell[0]] = 1
+        assert O.cast_bresenham(g, pose, R)[0] == np.float32(R), cell
 
 
 def _edt_brute(g):
