@@ -648,6 +648,14 @@ def test_motion_model_pins():
     assert np.allclose(a, b, atol=1e-6)
     th = np.float64(np.float32(1.0))
     assert np.isclose(a[0, 0], 5.0 + 1.5 * np.cos(th) - 0.75 * np.sin(th), atol=1e-5)
+    # a turn below 0 wraps up by one turn
+    out = O.motion(np.array([[1.0, 1.0, 0.1]], np.float32), [0, 1], np.array([[0.0, 0.0, -0.3]], np.float32), z[:1])
+    assert np.isclose(out[0, 2], np.float32(0.1) - np.float32(0.3) + 2 * np.pi, atol=1e-6)
+    # each filter segment (one of them empty) moves by its own odometry
+    q = np.array([[0.0, 0.0, 0.0]] * 5, np.float32)
+    out = O.motion(q, [0, 2, 2, 5], np.array([[1.0, 0, 0], [9.0, 0, 0], [3.0, 0, 0]], np.float32),
+                   np.zeros((5, 3), np.float32))
+    assert list(out[:, 0]) == [1.0, 1.0, 3.0, 3.0, 3.0]
 
 
 def test_resampling_pins():
@@ -658,6 +666,10 @@ def test_resampling_pins():
     n = 50
     idx, _ = O.resample_indices(np.full(n, -3.0, np.float32), [0, n], np.array([0.37], np.float32))
     assert np.array_equal(idx, np.arange(n))
+    # offset 0 and n a power of two: every target (m / n of the total) equals
+    # a running sum exactly, and the first sum above it is particle m's own
+    idx, _ = O.resample_indices(np.full(64, -3.0, np.float32), [0, 64], np.array([0.0], np.float32))
+    assert np.array_equal(idx, np.arange(64))
     lw = np.full(n, -np.inf, np.float32)
     lw[17] = -5.0
     idx, _ = O.resample_indices(lw, [0, n], np.array([0.9], np.float32))
@@ -675,6 +687,10 @@ def test_resampling_pins():
         expect = (b - a) * w / w.sum()
         cnt = np.bincount(k, minlength=b - a)
         assert (np.abs(cnt - expect) < 1.0 + 1e-9).all()
+    # only relative weights matter: a common shift of every log-weight, even
+    # one far beyond exp's range, draws the same particles
+    idx2, _ = O.resample_indices(lw + np.float32(1000.0), seg, u)
+    assert np.array_equal(idx2, idx)
 
 
 def test_lookup_table_pins(oracle):
@@ -697,6 +713,19 @@ def test_lookup_table_pins(oracle):
     got = O.lut_lookup(d.params, tab, mr, poses)
     assert got[0] == np.float32(tab[k, j, i]) / np.float32(sc) == got[1]
     assert got[2] == 0.0
+    # any pose inside a cell reads its state: the O1 brute-force cast from
+    # the cell centre in direction theta_k, coded
+    rs = synth.Stream(19)
+    m = 300
+    ii, jj, kk = rs.integers(m, 0, 47), rs.integers(m, 0, 39), rs.integers(m, 0, N - 1)
+    ths = np.array([np.float32(2.0 * np.pi * t / N) for t in kk], np.float32)
+    centre = np.stack([ii, jj, ths], 1).astype(np.float32)
+    jit = (rs.uniform(2 * m, -0.45, 0.45).reshape(m, 2)).astype(np.float32)
+    q = centre.copy()
+    q[:, :2] += jit
+    want = np.clip(np.floor(d.params.calc_range_brute(g, centre) * np.float32(sc) + np.float32(0.5)), 0, 65535)
+    got = O.lut_lookup(d.params, tab, mr, q)
+    assert np.array_equal(got, (want / np.float32(sc)).astype(np.float32))
 
 
 # ------------------------------------------------------------------ baselines
