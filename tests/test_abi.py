@@ -130,3 +130,21 @@ def test_trace_host_side(lib):
         assert cddt.trace_report() == []
     finally:
         assert lib.cddt_trace_enable(0) == cddt.CDDT_OK
+
+
+def test_c_example_builds_and_runs_without_a_device(tmp_path):
+    """The C ABI from plain C: tests/c_example/cddt_example.c compiles with gcc
+    against include/cddt.h and libcddt.so; without a CUDA device it checks the
+    argument and no-device statuses and exits 2."""
+    import subprocess
+
+    import torch
+
+    from tests.c_example.build_example import build_example
+    exe = build_example(str(tmp_path))
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    if torch.cuda.is_available():
+        assert r.returncode == 0, r.stdout + r.stderr
+    else:
+        assert r.returncode == 2, r.stdout + r.stderr
+        assert "no CUDA device" in r.stdout
