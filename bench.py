@@ -68,7 +68,7 @@ WORKLOAD_TEXT = {
 
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -85,11 +85,12 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms",
+                                          os.environ.get("CDDT_CLOCKS_MS", "200")],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(0.2)
         return self
 
     def __exit__(self, *a):
@@ -101,28 +102,43 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
-    def summary(self):
+    def summary(self, window=None):
+        """Median SM clock and active throttle reasons over the samples taken
+        inside `window` (wall-clock start and end of the timed region); when
+        the region is shorter than the sampling period and holds none, over
+        the last sample before it and the first after it (said in "basis")."""
+        import datetime
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
+            if len(p) < 10:
                 continue
             try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
+                t = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((t, float(p[2]), float(p[3]),
+                             [n for n, v in zip(names, p[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for n, v in zip(names, p[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        load = [s for s in sm if s > 0.5 * max(sm)] or sm
-        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        basis = "all samples"
+        use = rows
+        if window is not None:
+            t0, t1 = window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if inside:
+                use, basis = inside, "samples inside the timed region"
+            else:
+                before = [r for r in rows if r[0] < t0][-1:]
+                after = [r for r in rows if r[0] > t1][:1]
+                if before or after:
+                    use, basis = before + after, "nearest samples before and after the timed region"
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted({n for r in use for n in r[3]}), "samples": len(use), "basis": basis,
+                "region_ms": None if window is None else round(1e3 * (window[1] - window[0]), 3)}
 
 
 # ------------------------------------------------------------------ roofline helpers
@@ -248,12 +264,14 @@ class Timer:
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         barrier(self.world)
         torch.cuda.synchronize()
+        t0 = time.time()
         for i in range(k):
             self.flush.fill_(float(i))
             ev[i][0].record(stream)
             fn()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        self.window = (t0, time.time())
         barrier(self.world)
         return [a.elapsed_time(b) for a, b in ev]
 
@@ -357,7 +375,7 @@ def bench_corridor(args, G, torch, dev, world, rank):
     rays_per_step = S * P * B
     with ClockSampler(dev.index) as clk:
         ms = timed(plan.run, args.steps, args.warmup)
-    clocks = clk.summary()
+    clocks = clk.summary(timed.window)
     ms_step = max_over_ranks(world, statistics.mean(ms))
     value = world * rays_per_step / (ms_step * 1e-3)
 
@@ -679,6 +697,7 @@ def bench_batched64(args, G, torch, dev, world, rank):
     rays = sum(f["particles"].shape[0] for f in filters) * bo.numel()
     with ClockSampler(dev.index) as clk:
         ms = timed(plan.launch_graph, args.steps, args.warmup)
+    clock_window = timed.window
     ms_step = max_over_ranks(world, statistics.mean(ms))
 
     def sequential():
@@ -688,7 +707,7 @@ def bench_batched64(args, G, torch, dev, world, rank):
     line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "batched64",
                      {"launch": f"persistent batched under a CUDA graph, autotuned {shape}",
                       "particles": rays // bo.numel()})
-    line.update({"gpu_launches": args.steps, "clocks": clk.summary(),
+    line.update({"gpu_launches": args.steps, "clocks": clk.summary(clock_window),
                  "sequential_rays_per_s": rays / (statistics.mean(ms_s) * 1e-3),
                  "batched_speedup_vs_sequential": statistics.mean(ms_s) / statistics.mean(ms),
                  "build_ms_total": sum(build_ms)})
