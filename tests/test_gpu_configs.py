@@ -97,6 +97,43 @@ def test_corridor2000_batched_plan(G, oracle, corridor):
     plan.close()
 
 
+def test_corridor2000_u16(G, oracle, corridor):
+    """The 16-bit store at full size (reading S7): the zero points, the
+    200 000-query sweep by tree and binary search, and the fused plan in its
+    autotuned shape on sampled particles, against the oracle's 16-bit CDDT."""
+    w, _ = corridor
+    o = oracle.OracleCDDT(w["grid"], w["theta_disc"], w["max_range"], u16=True)
+    d = G.CDDT(dev(w["grid"]), w["theta_disc"], w["max_range"], u16=True)
+    _, bs, zp = d.export()
+    obs_, ozp = o.export()
+    assert np.array_equal(bs, obs_)
+    assert bits_equal(zp, ozp)
+    q = w["sweep"]
+    want = o.calc_range(q, nthreads=16)
+    qd = dev(q)
+    assert bits_equal(d.calc_range_many(qd).cpu().numpy(), want)
+    d.set_search(G.SEARCH_BINARY)
+    assert bits_equal(d.calc_range_many(qd).cpu().numpy(), want)
+    d.set_search(G.SEARCH_TREE)
+    S, P = w["parts"].shape[:2]
+    parts = dev(w["parts"].reshape(-1, 3))
+    bo = dev(w["beam_off"])
+    obs = dev(w["obs"])
+    logw = torch.full((S * P,), float("nan"), device="cuda")
+    m = G.beam_model(w["max_range"])
+    plan = G.Plan([dict(map=d, particles=parts[t * P:(t + 1) * P], beam_off=bo, obs=obs[t], model=m,
+                        logw=logw[t * P:(t + 1) * P], pair_offset=w["D"]) for t in range(S)])
+    plan.autotune()
+    plan.run()
+    got = logw.cpu().numpy().reshape(S, P)
+    om = oracle.beam_model(w["max_range"])
+    for t in range(3, S, 11):
+        idx = np.arange(t % 41, P, 41)
+        want = o.sensor_weights(w["parts"][t][idx], w["beam_off"], w["obs"][t], om, nthreads=16)
+        assert logw_close(got[t][idx], want), t
+    plan.close()
+
+
 def test_corridor2000_pruned(G, oracle, corridor):
     w, o = corridor
     d = G.CDDT(dev(w["grid"]), w["theta_disc"], w["max_range"])
