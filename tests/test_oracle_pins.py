@@ -913,3 +913,29 @@ def test_raymarch_against_exact_caster(oracle):
             iy = np.floor(py + ey_ + 0.5).astype(np.int64).clip(0, g.shape[0] - 1)
             ok |= occ[iy, ix]
     assert ok.all()
+
+
+def test_approximation_error_falls_with_theta_disc(oracle):
+    """The CDDT approximates the exact cast (Section II: discrete directions,
+    cells as rotated squares): on a corridor map its error against the exact
+    voxel-traversal caster (same query heading, distance to the first
+    crossed cell's centre projection) falls as theta_disc grows, in median
+    and at the 90th percentile, and at theta_disc >= 108 under 4 % of the
+    rays are off by more than 10 cells (rays grazing a door jamb or corner,
+    which the finer direction does not remove).  A report as much as a pin:
+    the values are listed with the design notes."""
+    g = synth.corridor_map(500, 500, r_min=48)
+    mr = 500.0
+    q = synth.uniform_queries(g, 20000, seed=71)
+    ex = oracle.cast_exact(g, q.astype(np.float64), mr, 0)
+    med, p90 = [], []
+    for N in (16, 36, 108, 360):
+        r = oracle.OracleCDDT(g, N, mr).calc_range(q).astype(np.float64)
+        d = np.abs(r - ex)
+        med.append(np.median(d))
+        p90.append(np.percentile(d, 90))
+        if N >= 108:
+            assert np.mean(d > 10) < 0.04, N
+    assert all(a > b for a, b in zip(med, med[1:])), med
+    assert all(a > b for a, b in zip(p90, p90[1:])), p90
+    assert med[-1] < 0.25 and p90[-1] < 1.5
