@@ -20,6 +20,14 @@
  *   O5  FP64 beam sensor model, its log-weight and its analytic gradient
  *   prune (Section IV-C) and incremental update (Section IV-D)
  *
+ * Parity unpinned: the choices the paper leaves open and no outside fact
+ * fixes -- lambda_short = 0.01 and the other beam-model constants, the
+ * truncated-normal option of p_hit, range 0 for an off-map query (S6), and
+ * the 16-bit scheme's Q and X_s (S7).  Every function below is pinned by the
+ * CPU tests to the paper's worked example, closed forms, library routines,
+ * brute force or invariants; these choices are only held equal on both
+ * sides.
+ *
  * Floating-point contract: the CDDT geometry is float32 with an explicit
  * operation order and no contraction (build with -ffp-contract=off); the
  * beam model is float64.  The readings taken where the paper is silent:

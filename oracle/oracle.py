@@ -3,6 +3,10 @@
 TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's
 CPU-baseline leg import this module.  The product path never does.
 
+Parity unpinned: the choices the paper leaves open (the beam-model constants
+such as lambda_short = 0.01, the truncated-normal option, range 0 off the map,
+the 16-bit Q and X_s); the functions themselves are pinned by the CPU tests.
+
 The C library is built with ``-O2 -ffp-contract=off`` so that float32
 expressions are evaluated one rounded operation at a time, exactly in the
 order written, on every host (GCC contracts a*b+c into an FMA by default on
