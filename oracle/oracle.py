@@ -3,6 +3,13 @@
 TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's
 CPU-baseline leg import this module.  The product path never does.
 
+Beside the C oracle's O1-O5, prune and update, this module holds plain
+NumPy forms of: the 16-bit lookup table's coding and lookups (reading L1),
+the motion model and low-variance resampling (readings M1, R1, float64), the
+sorted-CSR sector count of the roofline, the baseline casters' direction
+rule (D1, through the C library) and the ray marcher's Euclidean distance
+transform (scipy's exact transform as a library step, reading RM1).
+
 Parity unpinned: the choices the paper leaves open (the beam-model constants
 such as lambda_short = 0.01, the truncated-normal option, range 0 off the map,
 the 16-bit Q and X_s); the functions themselves are pinned by the CPU tests.
