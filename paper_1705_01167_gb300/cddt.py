@@ -19,7 +19,8 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-CDDT_OK, CDDT_ERR_ARG, CDDT_ERR_CUDA, CDDT_ERR_OOM, CDDT_ERR_PRUNED, CDDT_ERR_TIMEOUT, CDDT_ERR_DEVICE = range(7)
+(CDDT_OK, CDDT_ERR_ARG, CDDT_ERR_CUDA, CDDT_ERR_OOM, CDDT_ERR_PRUNED, CDDT_ERR_TIMEOUT, CDDT_ERR_DEVICE,
+ CDDT_ERR_BOUNDS) = range(8)
 CDDT_ZP_U16 = 1
 SEARCH_TREE, SEARCH_BINARY = 0, 1
 

@@ -39,8 +39,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_status_strings(lib):
     from paper_1705_01167_gb300 import cddt
-    for s in range(7):
+    for s in range(8):
         assert len(cddt.status_string(s)) > 0
+        assert "unknown" not in cddt.status_string(s), s
     assert "unknown" in cddt.status_string(99)
 
 
@@ -71,6 +72,21 @@ def test_host_side_argument_errors(lib):
     assert lib.cddt_import(fake, 10, 10, 7, 10.0, 0, 0, 2, bs, zp, None, C.byref(h)) == ARG
     assert lib.cddt_import(None, 10, 10, 8, 10.0, 0, 0, 2, bs, zp, None, C.byref(h)) == ARG
     assert lib.cddt_import(fake, 10, 10, 8, 10.0, 0, 0, 2, bs, zp, None, None) == ARG
+    # the comparison casters and the filter step
+    assert lib.cddt_cast_bresenham(None, fake, fake, 1, None) == ARG
+    assert lib.cddt_lut_build(None, None, C.byref(h)) == ARG
+    assert lib.cddt_lut_info(None, None, None) == ARG
+    assert lib.cddt_lut_calc_range_many(None, fake, fake, 1, None) == ARG
+    assert lib.cddt_lut_destroy(None) == cddt.CDDT_OK
+    assert lib.cddt_rm_build(None, None, C.byref(h)) == ARG
+    assert lib.cddt_rm_build(fake, None, None) == ARG
+    assert lib.cddt_rm_distances(None, None, None) == ARG
+    assert lib.cddt_rm_calc_range_many(None, fake, fake, None, 1, None) == ARG
+    assert lib.cddt_rm_destroy(None) == cddt.CDDT_OK
+    assert lib.cddt_motion(fake, -1, fake, 1, fake, fake, None) == ARG
+    assert lib.cddt_motion(fake, 1, fake, 0, fake, fake, None) == ARG
+    assert lib.cddt_resample(fake, fake, fake, 0, fake, C.c_void_p(0x2000), None, fake, None) == ARG
+    assert lib.cddt_resample(fake, fake, fake, 1, fake, fake, None, fake, None) == ARG  # out == particles
 
 
 def test_host_fault_injection(lib, monkeypatch):

@@ -61,7 +61,7 @@ for u16 in (False, True):
         r = d.calc_range_many(q)
         torch.cuda.synchronize()
         st = d.status()
-        assert st == 7, (u16, s, st)            # CDDT_ERR_BOUNDS
+        assert st == G.CDDT_ERR_BOUNDS, (u16, s, st)
         assert d.status() == 0                  # read and cleared
         assert torch.isfinite(r).all()
     d.close()
