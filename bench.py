@@ -9,7 +9,15 @@ theta_disc = 200, max range 1000 cells.  A ground-truth pose random-walks for
 launch; the CDDT (288 MB with its search trees) is resident in HBM and L2
 is flushed (a 256 MB write) between steps.  Extra keys report the same work
 as 200 per-filter launches, as a CUDA graph, with the binary-search layout,
-on the pruned CDDT, and a 10 M-query calc_range_many sweep.
+on the pruned CDDT and on the 16-bit store, with uniform particles, as a
+full filter step (motion, sensor model, resampling), end to end from
+page-locked host buffers, a 10 M-query random and a 50 M-state grid sweep
+with per-warp latency, the paper's comparison casters (lookup table, ray
+marching, Bresenham) on both samples (`methods`), and the CPU oracle.
+`clocks` summarises timestamped nvidia-smi samples (every 200 ms, or
+CDDT_CLOCKS_MS; raw samples kept in CDDT_CLOCKS_DIR when set) over the
+timed region, or the nearest ones when the region is shorter than the
+sampling period (`clocks.basis`).
 
 Other workloads (same JSON line, `config.name` names them):
   rects256      256 x 256 rectangles, theta_disc 108: one 1000-particle filter
