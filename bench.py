@@ -854,7 +854,8 @@ def run_profile(args):
     from paper_1705_01167_gb300 import cddt as G
     w = WL.corridor2000()
     dev = torch.device("cuda", 0)
-    d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], w["max_range"])
+    d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], w["max_range"],
+               u16=args.profile_case == "u16")
     bo, D = w["beam_off"], w["D"]
     S, P = w["parts"].shape[:2]
     r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], bo)).to(dev)).cpu().numpy()
@@ -888,8 +889,9 @@ def main():
     ap.add_argument("--workload", default="corridor2000", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
-    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "update"],
-                    help="--profile workload: the corridor plan, or 10^4-write updates on the 4000^2 map")
+    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "u16", "update"],
+                    help="--profile workload: the corridor plan (u16: on the 16-bit store), or 10^4-write "
+                         "updates on the 4000^2 map")
     ap.add_argument("--shape-tpp", type=int, default=1)
     ap.add_argument("--shape-ppi", type=int, default=512)
     ap.add_argument("--shape-block", type=int, default=512)
