@@ -164,3 +164,22 @@ def test_c_example_builds_and_runs_without_a_device(tmp_path):
     else:
         assert r.returncode == 2, r.stdout + r.stderr
         assert "no CUDA device" in r.stdout
+
+
+def test_no_cpu_fallback():
+    """Without the built library the binding raises instead of computing
+    anything itself, and host tensors are refused: there is no CPU path."""
+    import subprocess
+    import sys
+
+    code = ("import paper_1705_01167_gb300.build as b, paper_1705_01167_gb300.cddt as G\n"
+            "b.LIB = '/nonexistent/libcddt.so'\n"
+            "try:\n    G.load(build_if_missing=False)\nexcept RuntimeError as e:\n    print('raised:', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    assert r.returncode == 0 and "raised: libcddt.so is not built" in r.stdout, r.stdout + r.stderr
+    import torch
+
+    from paper_1705_01167_gb300 import cddt
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        cddt.CDDT(torch.zeros((8, 8), dtype=torch.uint8), 8, 10.0)
