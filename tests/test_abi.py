@@ -183,3 +183,16 @@ def test_no_cpu_fallback():
     from paper_1705_01167_gb300 import cddt
     with pytest.raises(ValueError, match="CUDA tensor"):
         cddt.CDDT(torch.zeros((8, 8), dtype=torch.uint8), 8, 10.0)
+
+
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    """include/cddt.h stands alone in C11 and C++17 translation units with
+    every warning an error (it needs only <stdint.h>)."""
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "use.c"
+    src.write_text('#include "cddt.h"\nint main(void) { return cddt_version() > 0 ? 0 : 1; }\n')
+    for cc, std, lang in (("gcc", "-std=c11", "c"), ("g++", "-std=c++17", "c++")):
+        r = subprocess.run([cc, std, "-x", lang, "-Wall", "-Wextra", "-Werror", "-pedantic", f"-I{inc}",
+                            "-fsyntax-only", str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, (cc, r.stderr)
