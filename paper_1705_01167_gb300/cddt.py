@@ -33,13 +33,15 @@ EXPORTED = (
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
     "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
     "cddt_lut_build", "cddt_lut_destroy", "cddt_lut_info", "cddt_lut_calc_range_many", "cddt_lut_sensor_weights",
-    "cddt_cast_bresenham", "cddt_checked_build", "cddt_trace_enable", "cddt_trace_report", "cddt_rm_build", "cddt_rm_destroy", "cddt_rm_distances", "cddt_rm_calc_range_many",
+    "cddt_cast_bresenham", "cddt_checked_build", "cddt_trace_enable", "cddt_trace_report",
+    "cddt_rm_build", "cddt_rm_destroy", "cddt_rm_distances", "cddt_rm_calc_range_many",
 )
 NOALLOC_MAX_QUERIES = 262144
 NOALLOC_MAX_THETA_DISC = 2048
 
 
 class CDDTError(RuntimeError):
+    """A failed C-ABI call: .status holds the cddt_status code."""
     def __init__(self, status: int, what: str):
         self.status = status
         super().__init__(f"{what}: {status_string(status)} (status {status})")
@@ -54,11 +56,13 @@ class BeamModel(C.Structure):
 
 def beam_model(max_range: float, z_hit=0.75, z_short=0.01, z_max=0.07, z_rand=0.12,
                sigma_hit=8.0, lambda_short=0.01, hit_truncnorm=0) -> BeamModel:
+    """The beam sensor model's parameters (reading S9) as the C struct, ranges in cells."""
     return BeamModel(z_hit, z_short, z_max, z_rand, sigma_hit, lambda_short, max_range,
                      int(hit_truncnorm))
 
 
 class Stats(C.Structure):
+    """cddt_stats: sizes and timings of a handle (cddt_get_stats)."""
     _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("theta_disc", C.c_int32),
                 ("n_slices", C.c_int32), ("max_range", C.c_float), ("flags", C.c_uint32),
                 ("pruned", C.c_int32), ("total_bins", C.c_int64), ("n_zero_points", C.c_int64),
@@ -66,16 +70,19 @@ class Stats(C.Structure):
                 ("build_ms", C.c_float), ("prune_ms", C.c_float), ("update_ms", C.c_float)]
 
     def as_dict(self):
+        """The fields as a dict."""
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Filter(C.Structure):
+    """cddt_filter: one filter of a plan (map handle, particles, scan, model, log-weights)."""
     _fields_ = [("map", C.c_void_p), ("particles_dev", C.c_void_p), ("P", C.c_int64),
                 ("beam_off_dev", C.c_void_p), ("obs_dev", C.c_void_p), ("B", C.c_int32),
                 ("pair_offset", C.c_int32), ("model", BeamModel), ("logw_dev", C.c_void_p)]
 
 
 def library_path() -> str:
+    """Path of the in-tree libcddt.so."""
     return _build.LIB
 
 
@@ -150,6 +157,7 @@ def load(build_if_missing: bool = True):
 
 
 def status_string(s: int) -> str:
+    """cddt_status_string: the text of a status code."""
     return load().cddt_status_string(s).decode()
 
 
@@ -262,9 +270,11 @@ class CDDT:
 
     @property
     def handle(self):
+        """The C handle (cddt_t) as a ctypes pointer."""
         return self._h
 
     def close(self):
+        """cddt_destroy: free the handle's device memory (idempotent)."""
         if getattr(self, "_h", None):
             load().cddt_destroy(self._h)
             self._h = None
@@ -277,10 +287,12 @@ class CDDT:
 
     # ---- maintenance
     def prune(self, stream=None):
+        """cddt_prune: drop the zero points no free-space query can return (Section IV-C)."""
         with torch.cuda.device(self.device):
             _check(load().cddt_prune(self._h, _stream(stream)), "cddt_prune")
 
     def update_cells(self, xy: torch.Tensor, occ: torch.Tensor, stream=None):
+        """cddt_update_cells: write cells (xy int32 [n, 2], occ uint8 [n]) into the map and the store (Section IV-D)."""
         _dev(xy, torch.int32, "xy")
         _dev(occ, torch.uint8, "occ")
         n = occ.numel()
@@ -291,15 +303,18 @@ class CDDT:
                    "cddt_update_cells")
 
     def set_search(self, search: int):
+        """cddt_set_search: SEARCH_TREE (the default) or SEARCH_BINARY over the same store."""
         _check(load().cddt_set_search(self._h, search), "cddt_set_search")
 
     def stats(self) -> dict:
+        """cddt_get_stats as a dict."""
         s = Stats()
         with torch.cuda.device(self.device):
             _check(load().cddt_get_stats(self._h, C.byref(s)), "cddt_get_stats")
         return s.as_dict()
 
     def status(self) -> int:
+        """cddt_get_status: the device status word (read and cleared)."""
         with torch.cuda.device(self.device):
             return load().cddt_get_status(self._h)
 
@@ -317,6 +332,7 @@ class CDDT:
         return sb, bs, zp[:bs[-1]].copy()
 
     def export_grid(self):
+        """cddt_export_grid: (grid, edge map) as uint8 [H, W] host arrays."""
         import numpy as np
         g = np.empty((self.H, self.W), np.uint8)
         e = np.empty((self.H, self.W), np.uint8)
@@ -328,6 +344,7 @@ class CDDT:
     # ---- queries
     def calc_range_many(self, poses: torch.Tensor, sort_by_slice: bool = False,
                         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """cddt_calc_range_many: ranges [n] of poses [n, 3] (optionally slice-sorted, same answers)."""
         _dev(poses, torch.float32, "poses")
         n = poses.numel() // 3
         if poses.numel() != 3 * n:
@@ -390,6 +407,7 @@ class CDDT:
 
     def sensor_weights(self, particles, beam_off, obs, model: BeamModel, pair_offset: int = 0,
                        want_ranges: bool = False, logw=None, stream=None):
+        """cddt_sensor_weights: log-weights [P] of particles [P, 3] (and the ranges [P, B] when asked)."""
         P, B = self._sensor_args(particles, beam_off, obs)
         if logw is None:
             logw = torch.empty(P, dtype=torch.float32, device=particles.device)
@@ -403,6 +421,7 @@ class CDDT:
 
     def sensor_weights_backward(self, particles, beam_off, obs, model: BeamModel, grad_logw,
                                 pair_offset: int = 0, grad_xy=None, stream=None):
+        """cddt_sensor_weights_backward: d(log w)/d(x, y) [P, 2] scaled by grad_logw [P]."""
         P, B = self._sensor_args(particles, beam_off, obs)
         _dev(grad_logw, torch.float32, "grad_logw")
         if grad_xy is None:
@@ -417,6 +436,7 @@ class CDDT:
 
     def sensor_weights_fwd_bwd(self, particles, beam_off, obs, model: BeamModel,
                                pair_offset: int = 0, logw=None, grad_xy=None, stream=None):
+        """cddt_sensor_weights_fwd_bwd: log-weights and their gradient in one pass."""
         P, B = self._sensor_args(particles, beam_off, obs)
         if logw is None:
             logw = torch.empty(P, dtype=torch.float32, device=particles.device)
@@ -450,6 +470,7 @@ class SensorWeights(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, particles, cddt: CDDT, beam_off, obs, model: BeamModel, pair_offset: int = 0):
+        """The forward pass: log-weights of the particles."""
         p = particles.detach().contiguous()
         logw = cddt.sensor_weights(p, beam_off, obs, model, pair_offset)
         ctx.save_for_backward(p)
@@ -458,6 +479,7 @@ class SensorWeights(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_logw):
+        """The adjoint: the gradient with respect to the particles' (x, y); theta gets 0."""
         (p,) = ctx.saved_tensors
         g = ctx.cddt.sensor_weights_backward(p, ctx.beam_off, ctx.obs, ctx.model,
                                              grad_logw.contiguous().float(), ctx.D)
@@ -491,11 +513,13 @@ class Lut:
         self.device = cddt.device
 
     def info(self):
+        """cddt_lut_info: {'bytes', 'scale'} of the table."""
         b, sc = C.c_int64(), C.c_float()
         _check(load().cddt_lut_info(self._h, C.byref(b), C.byref(sc)), "cddt_lut_info")
         return {"bytes": b.value, "scale": sc.value}
 
     def calc_range_many(self, poses: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """cddt_lut_calc_range_many: ranges [n] read from the table at each pose's state."""
         _dev(poses, torch.float32, "poses")
         n = poses.numel() // 3
         if out is None:
@@ -523,6 +547,7 @@ class Lut:
         return logw
 
     def close(self):
+        """cddt_lut_destroy (idempotent)."""
         if getattr(self, "_h", None):
             load().cddt_lut_destroy(self._h)
             self._h = None
@@ -603,6 +628,7 @@ class RayMarch:
         return out
 
     def close(self):
+        """cddt_rm_destroy (idempotent)."""
         if getattr(self, "_h", None):
             load().cddt_rm_destroy(self._h)
             self._h = None
@@ -682,26 +708,32 @@ class Plan:
         self._h = h
 
     def autotune(self, stream=None):
+        """cddt_plan_autotune: time the candidate launch shapes on the plan's own work, keep the fastest."""
         _check(load().cddt_plan_autotune(self._h, _stream(stream)), "cddt_plan_autotune")
         return self.shape()
 
     def set_shape(self, tpp: int, ppi: int, block: int, regcap: int = 0):
+        """cddt_plan_set_shape: lanes per particle, particles per item, block size, register cap."""
         _check(load().cddt_plan_set_shape(self._h, tpp, ppi, block, regcap), "cddt_plan_set_shape")
 
     def shape(self):
+        """cddt_plan_get_shape as a dict."""
         a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         _check(load().cddt_plan_get_shape(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
                "cddt_plan_get_shape")
         return {"tpp": a.value, "ppi": b.value, "block": c.value, "regcap": d.value}
 
     def run(self, stream=None):
+        """cddt_plan_run: weight every filter of the plan in one persistent launch per key type."""
         _check(load().cddt_plan_run(self._h, _stream(stream)), "cddt_plan_run")
 
     def launch_graph(self, stream=None):
+        """cddt_plan_launch_graph: the same as a CUDA graph (captured on first use)."""
         _check(load().cddt_plan_launch_graph(self._h, _stream(stream)), "cddt_plan_launch_graph")
 
     @property
     def items(self) -> int:
+        """cddt_plan_items: work items of the plan."""
         return load().cddt_plan_items(self._h)
 
     def groups(self):
@@ -712,6 +744,7 @@ class Plan:
         return tuple(int(v) for v in out)
 
     def close(self):
+        """cddt_plan_destroy (idempotent)."""
         if getattr(self, "_h", None):
             load().cddt_plan_destroy(self._h)
             self._h = None
