@@ -635,7 +635,10 @@ def bench_corridor(args, G, torch, dev, world, rank):
                      "kernel": "batched_kernel", "algorithmic_bytes_per_launch": alg, "work": work,
                      "sector_bytes_per_launch": sec, "sector_gbs": sec / (ms_step * 1e-3) / 1e9,
                      "gather_gbs_measured": gbw,
-                     "sector_frac_of_hbm_gather": sec / (ms_step * 1e-3) / 1e9 / gbw["hbm"]},
+                     "sector_frac_of_hbm_gather": sec / (ms_step * 1e-3) / 1e9 / gbw["hbm"],
+                     "limiter": ("on-chip: L1 data-pipe wavefronts and instruction issue (ncu, "
+                                 "profiles/batched_kernel_corridor2000.md); the tracking filter's "
+                                 "gathers are cache resident, DRAM traffic ~1 % of the algorithmic bytes")},
         "e2e": {"value": world * rays_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(parts_h.numel() * 4 + obs_h.numel() * 4),
                 "d2h_bytes_per_step": int(logw_h.numel() * 4),
