@@ -399,7 +399,9 @@ typedef struct cddt_rm_s *cddt_rm;
  * exact integer squared distance; W + H everywhere on a map without an
  * occupied cell.  4 * W * H bytes of device memory owned by the object, plus
  * 2 * W * H bytes of scratch during the build (stream-ordered).  Keeps h's
- * max_range.  Errors: ARG (NULL, or h not on the current device), OOM, CUDA. */
+ * max_range.  The transform is written on `stream`: a caller that uses it on
+ * another stream synchronises first.  Errors: ARG (NULL, or h not on the
+ * current device), OOM, CUDA. */
 CDDT_API cddt_status cddt_rm_build(cddt_t h, void *stream, cddt_rm *out);
 CDDT_API cddt_status cddt_rm_destroy(cddt_rm r);
 /* The transform's device pointer (owned by r, valid until destroy) and its
@@ -430,7 +432,8 @@ typedef struct cddt_lut_s *cddt_lut;
  * current store): uint16 [N][H][W], entry = round-half-up(range * scale),
  * scale = the largest power of two with max_range * scale <= 65535, so the
  * range read back is code / scale.  2 * W * H * N bytes of device memory,
- * owned by the table.  Errors: ARG, OOM, CUDA. */
+ * owned by the table.  The table is written on `stream`: a caller that reads
+ * it on another stream synchronises first.  Errors: ARG, OOM, CUDA. */
 CDDT_API cddt_status cddt_lut_build(cddt_t h, void *stream, cddt_lut *out);
 CDDT_API cddt_status cddt_lut_destroy(cddt_lut l);
 /* Table bytes and scale; either pointer may be NULL.  Errors: ARG. */
