@@ -646,7 +646,7 @@ def bench_corridor(args, G, torch, dev, world, rank):
                 "copy_engine_value": world * rays_per_step / (copy_ms * 1e-3)},
         "gpu_launches": args.steps, "clocks": clocks,
         "build_ms": st0["build_ms"], "build_wall_s": build_wall, **extra})
-    if not args.no_cpu and rank == 0:
+    if not args.no_cpu and rank == 0 and world == 1:
         from oracle import oracle as O
         cores = os.cpu_count() or 1
         o = O.OracleCDDT(w["grid"], w["theta_disc"], mr)
