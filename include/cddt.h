@@ -132,10 +132,12 @@ CDDT_API cddt_status cddt_update_cells(cddt_t h, const int32_t *xy_dev, const ui
  * pose_dev float [n][3] = (x, y, theta) -> range_dev float [n].  A query whose
  * nearest cell is occupied or off the map returns 0; a ray that meets no
  * zero point returns max_range.  sort_by_slice != 0 first orders the queries
- * by slice (a counting sort on the device) so that the gathers of one slice
- * run together; the answers are the same.  scratch: with sort_by_slice the
- * handle keeps an internal scratch of 8 bytes per query (grown on demand;
- * growing synchronises `stream`).  Errors: ARG, CUDA, OOM. */
+ * by slice and direction (a counting sort on the device) so that the gathers
+ * of one slice run together and reach DRAM about once per slice; the answers
+ * are the same.  scratch: with sort_by_slice the handle keeps an internal
+ * scratch of 16 bytes per query plus 4 bytes per (bucket, sort block) --
+ * at most 1024 buckets, two per stored slice, and a few hundred blocks --
+ * grown on demand (growing synchronises `stream`).  Errors: ARG, CUDA, OOM. */
 CDDT_API cddt_status cddt_calc_range_many(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
                                  int32_t sort_by_slice, void *stream);
 
@@ -154,7 +156,7 @@ CDDT_API cddt_status cddt_calc_range_timed(cddt_t h, const float *pose_dev, floa
  * memory up front and gives libraries fixed budgets, or a real-time loop that
  * forbids allocation after start-up.  It returns the same ranges as
  * cddt_calc_range_many(h, pose_dev, range_dev, n, 1, stream), but keeps its
- * scratch in one fixed buffer of about 7.3 MB that is part of the library's
+ * scratch in one fixed buffer of about 4.7 MB that is part of the library's
  * device image (held on every device that loads the library until the
  * process exits) instead of memory the handle allocates.
  *   n            0 .. CDDT_NOALLOC_MAX_QUERIES queries (float [n][3] poses,
@@ -163,7 +165,9 @@ CDDT_API cddt_status cddt_calc_range_timed(cddt_t h, const float *pose_dev, floa
  * Larger inputs return CDDT_ERR_ARG without launching anything.
  * The first call on a device looks up the buffer's device address (a
  * one-time set-up per device, under a lock); make that first call before any
- * stream capture.  Every call shares the one buffer, which keeps the last
+ * stream capture.  The address is kept for the life of the process, so the
+ * entry point is not valid on a device after cudaDeviceReset of that device
+ * (the reset discards the buffer the address points to).  Every call shares the one buffer, which keeps the last
  * call's contents (nothing in it needs to start at zero): calls whose GPU
  * work overlaps -- on different streams, or from different threads -- race
  * on it, so the caller must order them.  The call calls no cudaMalloc,

@@ -84,7 +84,7 @@ extern "C" cddt_status cddt_cast_bresenham(cddt_t h, const float *pose_dev, floa
     if (!h || n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_cast_bresenham");
     if (n == 0) return CDDT_OK;
-    cddt::bresenham_kernel<<<cddt::grid_cap(n, 256, 152 * 64), 256, 0, (cudaStream_t)stream>>>(
+    cddt::bresenham_kernel<<<cddt::grid_cap(n, 256, 64), 256, 0, (cudaStream_t)stream>>>(
         h->grid, h->W, h->H, pose_dev, range_dev, n, h->max_range);
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;

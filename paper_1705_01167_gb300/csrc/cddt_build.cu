@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -25,6 +26,23 @@ cddt_status cuda_status(cudaError_t e)
 {
     if (e == cudaErrorMemoryAllocation) return CDDT_ERR_OOM;
     return CDDT_ERR_CUDA;
+}
+
+int sm_count()
+{
+    constexpr int kDevices = 64;
+    static std::atomic<int> cached[kDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev >= kDevices) {
+        int v = 0;
+        return cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0 ? v : 1;
+    }
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+    cached[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 // ------------------------------------------------------------ scan
@@ -259,7 +277,7 @@ __global__ void scatter_kernel(const uint32_t *cells, int64_t E, int W, const Sl
 static unsigned grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
-    if (b > 152 * 64) b = 152 * 64;
+    if (b > (int64_t)sm_count() * 64) b = (int64_t)sm_count() * 64;
     if (b < 1) b = 1;
     return (unsigned)b;
 }
@@ -592,14 +610,14 @@ cddt_status sort_segments(const Segs<KT> &sg, int64_t nseg, cudaStream_t st, Are
     if (cnt[0]) warp_sort_kernel<KT><<<grid_for((int64_t)cnt[0] * 32, 256), 256, 0, st>>>(sg, L, cnt[0]);
     if (cnt[1]) {  // 1025..2048 keys: 128 threads x 16 keys
         const size_t sm = sizeof(KT) * kBlockSortMax;
-        block_reg_sort_kernel<KT, kBlockSortMax / 16><<<std::min<uint32_t>(cnt[1], 152 * 16), kBlockSortMax / 16, sm, st>>>(
+        block_reg_sort_kernel<KT, kBlockSortMax / 16><<<std::min<uint32_t>(cnt[1], (uint32_t)sm_count() * 16), kBlockSortMax / 16, sm, st>>>(
             sg, L + nseg, cnt[1]);
     }
     if (cnt[2]) {  // 2049..16384 keys: 1024 threads x 16 keys
         const size_t sm = sizeof(KT) * kBigSortMax;
         CDDT_CUDA(cudaFuncSetAttribute(block_reg_sort_kernel<KT, kBigSortMax / 16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        block_reg_sort_kernel<KT, kBigSortMax / 16><<<std::min<uint32_t>(cnt[2], 152 * 2), kBigSortMax / 16, sm, st>>>(
+        block_reg_sort_kernel<KT, kBigSortMax / 16><<<std::min<uint32_t>(cnt[2], (uint32_t)sm_count() * 2), kBigSortMax / 16, sm, st>>>(
             sg, L + 2 * nseg, cnt[2]);
     }
     if (cnt[3]) {

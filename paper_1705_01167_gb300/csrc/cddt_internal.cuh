@@ -201,6 +201,16 @@ __device__ __forceinline__ bool query_dir(float theta, float inv_step, int N, in
     return true;
 }
 
+// Index of the cell nearest (x, y) in the grid, -1 off the map or for a
+// non-finite coordinate (the cell test of the occupancy pre-check).
+__device__ __forceinline__ int64_t map_cell(int W, int H, float x, float y)
+{
+    const float fx = floorf(__fadd_rn(x, 0.5f));
+    const float fy = floorf(__fadd_rn(y, 0.5f));
+    if (!(fx >= 0.0f && fx < (float)W && fy >= 0.0f && fy < (float)H)) return -1;
+    return (int64_t)(int)fy * W + (int)fx;
+}
+
 // Occupancy pre-check (Section IV-C): the query may be cast only from a free,
 // in-map cell.
 __device__ __forceinline__ bool free_cell(const uint8_t *grid, int W, int H, float x, float y)
@@ -358,6 +368,17 @@ __device__ __forceinline__ uint64_t policy_evict_last()
     uint64_t pol = 0;
 #if CDDT_LD_HINT
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#endif
+    return pol;
+}
+
+// The default L2 priority, for casts whose gathers move through the store
+// one slice at a time (nothing should outlive its slice in L2).
+__device__ __forceinline__ uint64_t policy_evict_normal()
+{
+    uint64_t pol = 0;
+#if CDDT_LD_HINT
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
 #endif
     return pol;
 }
@@ -1006,6 +1027,10 @@ struct cddt_s {
 // Host helpers shared by the translation units.
 namespace cddt {
 cddt_status cuda_status(cudaError_t e);
+// Streaming multiprocessors of the current device, queried once per device
+// and cached (cddt_build.cu).  Grid caps are multiples of it; when the query
+// fails it returns 1, which only narrows a grid-stride launch.
+int sm_count();
 // Build the sorted, tree-indexed store from per-bin key lists; implemented in
 // cddt_build.cu and reused by prune and update.
 cddt_status build_index(cddt_s *h, cudaStream_t st);

@@ -51,6 +51,13 @@ cddt_status launch_sensor(const cddt_s *h, const SensorArgs &a, int mode, cudaSt
 cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int sorted, cudaStream_t st);
 cddt_status calc_range_timed(cddt_s *h, const float *pose, float *out, int64_t n, long long *cycles,
                              cudaStream_t st);
+// The slice sort of cddt_calc_range_many (cddt_query.cu): blocks of
+// kSortThreads threads place tiles of kSortTile queries; slices are grouped
+// into at most kMaxSortBuckets buckets.
+constexpr int kSortThreads = 512;
+constexpr int kSortPerThread = 4;
+constexpr int kSortTile = kSortThreads * kSortPerThread;
+constexpr int kMaxSortBuckets = 1024;
 // The slice-sorted cast on caller-provided scratch of sorted_scratch_bytes(h, n)
 // bytes (cddt_query.cu); returns CDDT_ERR_ARG when the scratch is too small.
 int64_t sorted_scratch_bytes(const cddt_s *h, int64_t n);
@@ -128,8 +135,11 @@ cddt_status index_store(cddt_s *h, cudaStream_t st);
 // projected coordinate.
 float prune_eps(int W, int H);
 
-inline unsigned grid_cap(int64_t n, int threads, int64_t cap = 152 * 64)
+// Blocks of a grid-stride launch over n items: one per `threads` items, at
+// most per_sm blocks per streaming multiprocessor.
+inline unsigned grid_cap(int64_t n, int threads, int64_t per_sm = 64)
 {
+    const int64_t cap = (int64_t)sm_count() * per_sm;
     int64_t b = (n + threads - 1) / threads;
     if (b > cap) b = cap;
     if (b < 1) b = 1;

@@ -149,7 +149,7 @@ cddt_status cddt_lut_build(cddt_t h, void *stream, cddt_lut *out)
     // the pageable source is consumed before the call returns
     cudaError_t ce = cudaMemcpyAsync(th, th_h.data(), sizeof(float) * th_h.size(), cudaMemcpyHostToDevice, st);
     const cddt::MapView m = h->view();
-    const unsigned blocks = cddt::grid_cap(n, 256, 152 * 64);
+    const unsigned blocks = cddt::grid_cap(n, 256, 64);
     const bool bin = h->search == CDDT_SEARCH_BINARY;
     if (ce == cudaSuccess) {
         if (h->u16 && bin)
@@ -195,7 +195,7 @@ cddt_status cddt_lut_calc_range_many(cddt_lut L, const float *pose_dev, float *r
     if (!L || n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_lut_calc_range_many");
     if (n == 0) return CDDT_OK;
-    cddt::lut_calc_range_kernel<<<cddt::grid_cap(n, 256, 152 * 64), 256, 0, (cudaStream_t)stream>>>(*L, pose_dev,
+    cddt::lut_calc_range_kernel<<<cddt::grid_cap(n, 256, 64), 256, 0, (cudaStream_t)stream>>>(*L, pose_dev,
                                                                                                    range_dev, n);
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;
@@ -211,7 +211,7 @@ cddt_status cddt_lut_sensor_weights(cddt_lut L, const float *particles_dev, int6
     if (!(m->sigma_hit > 0) || !(m->max_range > 0) || !(m->lambda_short > 0)) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_lut_sensor_weights");
     if (P == 0) return CDDT_OK;
-    cddt::lut_sensor_kernel<<<cddt::grid_cap(P, 256, 152 * 64), 256, 0, (cudaStream_t)stream>>>(
+    cddt::lut_sensor_kernel<<<cddt::grid_cap(P, 256, 64), 256, 0, (cudaStream_t)stream>>>(
         *L, particles_dev, P, seg_start_dev, F, beam_off_dev, obs_dev, B, cddt::make_beam_consts(*m), logw_dev);
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;

@@ -159,7 +159,7 @@ static cddt_status prune_kt(cddt_s *h, cudaStream_t st)
     CDDT_CUDA(old_hdr.alloc(sizeof(BinHdr) * (size_t)std::max<int64_t>(nb, 1)));
     CDDT_CUDA(cudaMemsetAsync(keep.p, 0, (size_t)h->store_nodes * K, st));
     const int64_t work = (int64_t)h->W * h->H * h->S;
-    prune_mark_kernel<KT><<<grid_cap(work, 256, 152 * 32), 256, 0, st>>>(h->view(), prune_eps(h->W, h->H),
+    prune_mark_kernel<KT><<<grid_cap(work, 256, 32), 256, 0, st>>>(h->view(), prune_eps(h->W, h->H),
                                                                           keep.as<uint8_t>(),
                                                                           h->store_nodes * K);
     count_kept_kernel<KT><<<grid_cap(nb * 32, 256), 256, 0, st>>>(h->hdr, nb, keep.as<uint8_t>(), cnt.as<uint32_t>());
@@ -695,7 +695,7 @@ static cddt_status update_kt(cddt_s *h, const int32_t *xy, const uint8_t *occ, i
     // per-bin insert / delete counts and offsets
     uint32_t *ins_n = arr, *del_n = ins_n + nb, *ins_off = del_n + nb, *del_off = ins_off + nb, *new_n = del_off + nb;
     CDDT_CUDA(cudaMemsetAsync(ins_n, 0, sizeof(uint32_t) * 2 * (size_t)nb, st));
-    const unsigned gd = grid_cap((int64_t)9 * n * h->S, 256, 152 * 32);
+    const unsigned gd = grid_cap((int64_t)9 * n * h->S, 256, 32);
     upd_delta_kernel<KT, 0><<<gd, 256, 0, st>>>(flips, nflips, h->W, h->slices, h->S, h->Q, ins_n, del_n, nullptr,
                                                 nullptr, nullptr, nullptr, nullptr, nullptr);
     exclusive_scan_u32(ins_n, ins_off, nb, scratch, tot, st);

@@ -134,7 +134,7 @@ cddt_status cddt_motion(float *particles_dev, int64_t P, const int64_t *seg_star
         return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_motion");
     if (P == 0) return CDDT_OK;
-    cddt::motion_kernel<<<cddt::grid_cap(P, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(
+    cddt::motion_kernel<<<cddt::grid_cap(P, 256, 16), 256, 0, (cudaStream_t)stream>>>(
         particles_dev, P, seg_start_dev, F, odom_dev, noise_dev);
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;

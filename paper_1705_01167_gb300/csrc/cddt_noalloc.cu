@@ -13,17 +13,19 @@
 
 #include "cddt_internal.cuh"
 #include "cddt_kernels.cuh"
+#include "cddt_trace.cuh"
 
 namespace {
 
 // Largest inputs the fixed buffer holds.
 constexpr int64_t kMaxQueries = CDDT_NOALLOC_MAX_QUERIES;
-constexpr int64_t kMaxBuckets = CDDT_NOALLOC_MAX_THETA_DISC / 2 + 1;
-constexpr int64_t kMaxBlocks = (kMaxQueries + 511) / 512;
+constexpr int64_t kMaxBuckets = cddt::kMaxSortBuckets;
+constexpr int64_t kMaxBlocks = (kMaxQueries + cddt::kSortTile - 1) / cddt::kSortTile;
 constexpr int64_t kMaxCounts = kMaxBuckets * kMaxBlocks;
-// scan scratch + counts + alignment + bucket + permutation + sorted poses
-constexpr size_t kScratchBytes =
-    8 * (kMaxCounts / 4096 + 4) + 4 * kMaxCounts + 16 + 4 * kMaxQueries + 4 * kMaxQueries + 12 * kMaxQueries;
+// scan partials and total + (bucket, block) counts + alignment + one
+// 16-byte record per query (the layout of the sorted path's scratch; the
+// call checks the exact size before it launches anything)
+constexpr size_t kScratchBytes = 8 * (kMaxCounts / 4096 + 4) + 4 * kMaxCounts + 16 + 16 * kMaxQueries;
 
 // The buffer itself.  Host code must not pass its name to a kernel (in host
 // code it is only a stand-in for the symbol); its device address comes from
@@ -53,18 +55,19 @@ cddt_status scratch_address(int dev, void **out)
 extern "C" cddt_status cddt_calc_range_many_noalloc(cddt_t h, const float *pose_dev, float *range_dev, int64_t n,
                                                     void *stream)
 {
+    CDDT_RANGE("cddt_calc_range_many_noalloc", stream);
     if (!h) return CDDT_ERR_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return CDDT_ERR_CUDA;
     if (dev != h->device) return CDDT_ERR_ARG;
     if (n < 0 || n > kMaxQueries || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
     if (h->N > CDDT_NOALLOC_MAX_THETA_DISC) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_calc_range_many_noalloc");
     void *scratch = nullptr;
     cddt_status rc = scratch_address(dev, &scratch);
     if (rc != CDDT_OK) return rc;
     if (n == 0) return CDDT_OK;
-    const int64_t need = cddt::sorted_scratch_bytes(h, n);
-    if (need < 0 || need > (int64_t)kScratchBytes) return CDDT_ERR_ARG;
+    if (cddt::sorted_scratch_bytes(h, n) > (int64_t)kScratchBytes) return CDDT_ERR_ARG;
     return cddt::calc_range_sorted_into(h, pose_dev, range_dev, n, scratch, (int64_t)kScratchBytes,
                                         (cudaStream_t)stream);
 }

@@ -40,7 +40,7 @@ extern "C" cddt_status cddt_gather_probe(const void *buf_dev, int64_t bytes, int
     if (!buf_dev || !sink_dev || bytes < 32 || (bytes & 31) || sectors < 0) return CDDT_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(buf_dev) & 31) return CDDT_ERR_ARG;  // 256-bit loads
     if (sectors == 0) return CDDT_OK;
-    const unsigned blocks = cddt::grid_cap(sectors, 256, 152 * 16);
+    const unsigned blocks = cddt::grid_cap(sectors, 256, 16);
     cddt::gather_probe_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
         reinterpret_cast<const char *>(buf_dev), (uint64_t)bytes >> 5, sectors, seed,
         reinterpret_cast<unsigned long long *>(sink_dev));

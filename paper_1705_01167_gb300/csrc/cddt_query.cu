@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -84,63 +85,274 @@ cddt_status calc_range_timed(cddt_s *h, const float *pose, float *out, int64_t n
     return CDDT_OK;
 }
 
-// Slice bucket of a query: its stored slice, or S when no search is needed.
-__device__ __forceinline__ int slice_bucket(const MapView &m, float x, float y, float th)
+// ------------------------------------------------------------ slice-sorted casts
+//
+// Section IV-C keeps one set of zero points per stored slice.  A batch
+// ordered by slice gathers from one slice's bins at a time (a 2000 x 2000
+// map's slice holds ~3 MB of its 288 MB store), so the bins a warp reads
+// were mostly brought into L2 by the queries just before it.  The order is
+// made by a counting sort on the device:
+//   count  per block of the batch, its queries of each bucket (a bucket is
+//          one direction of one stored slice, or 2^sh consecutive ones when
+//          they outnumber kMaxSortBuckets).  The bucket depends on the
+//          heading alone, so this pass reads the poses and nothing else;
+//   scan   bucket-major exclusive scan of the (bucket, block) counts: the
+//          first slot of each block's queries of each bucket;
+//   place  each block re-reads its queries a tile at a time, applies the
+//          occupancy pre-check, groups the tile by bucket in shared memory
+//          and writes one 16-byte record per query, {x, y, query index,
+//          slice | flags}, consecutive threads to consecutive slots;
+//   cast   one thread per record, in record order: project into the slice
+//          (the float32 steps of the unsorted cast), search the bin and
+//          write the range to the query's output slot.
+// Poses move in 16-byte loads through shared memory (a tile of kSortTile
+// poses is 24 KB) whenever the batch starts on a 16-byte boundary.
+// Record flags (high bits of its last word, below them the stored slice).
+constexpr uint32_t kRecReverse = 0x80000000u;  // search backwards (direction k >= N/2)
+constexpr uint32_t kRecZero = 0x40000000u;     // occupied or off-map cell, non-finite pose: range 0
+constexpr uint32_t kRecSlice = 0x3fffffffu;
+
+// Sort bucket of a heading: (2 slice + reverse) >> sh, so that the two
+// directions of a slice are neighbouring buckets and a warp's records search
+// one way (-1 for a non-finite heading, which goes to bucket 0 with a record
+// of range 0).
+__device__ __forceinline__ int sort_bucket(const MapView &m, float th, int sh, int &s, bool &rev)
 {
-    if (!free_cell(m.grid, m.W, m.H, x, y)) return m.S;
     int k;
-    if (!query_dir(th, m.inv_step, m.N, k)) return m.S;
-    return k >= m.S ? k - m.S : k;
+    if (!query_dir(th, m.inv_step, m.N, k)) {
+        s = 0;
+        rev = false;
+        return -1;
+    }
+    rev = k >= m.S;
+    s = rev ? k - m.S : k;
+    return ((s << 1) | (rev ? 1 : 0)) >> sh;
 }
 
-// Counting sort of queries by slice, in three passes over fixed chunks (one
-// chunk per block): per-chunk histograms in shared memory, an exclusive scan
-// of the bucket-major (bucket, chunk) counts, then a placement pass that
-// writes the permutation and the poses in slice order.
-constexpr int kSortThreads = 512;
-
-__global__ void bucket_count_kernel(MapView m, const float *pose, int64_t n, int64_t chunk, uint32_t *bucket,
-                                    uint32_t *counts, int nbk)
+// Asynchronous copy of 16 bytes from global to shared memory (cp.async,
+// completed by cp_async_wait).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
-    extern __shared__ uint32_t hist[];
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Start copying the poses of queries [t0, t0 + cnt) (cnt <= kSortTile) into
+// sp[3 cnt], by the whole block: asynchronous 16-byte copies when the tile
+// starts on a 16-byte boundary (its last few floats, and every float of an
+// unaligned tile, by plain loads).  Complete after cp_async_wait and a
+// barrier.
+__device__ __forceinline__ void load_pose_tile(const float *pose, int64_t t0, int cnt, float *sp)
+{
+    const float *src = pose + 3 * t0;
+    const int nf = 3 * cnt;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int n4 = nf >> 2;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) cp_async16(sp + 4 * i, src + 4 * i);
+        done = n4 << 2;
+    }
+    for (int i = done + threadIdx.x; i < nf; i += blockDim.x) sp[i] = __ldg(src + i);
+    cp_async_commit();
+}
+
+// Bytes of one tile's poses.
+constexpr int kPoseBuf = 3 * (int)sizeof(float) * kSortTile;
+
+__global__ void __launch_bounds__(kSortThreads) sort_count_kernel(MapView m, const float *pose, int64_t n,
+                                                                  int64_t chunk, int sh, int nbk, uint32_t *counts)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    // pose buffer i & 1 of tile i at smem + (i & 1) * kPoseBuf
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + 2 * kPoseBuf);
     for (int b = threadIdx.x; b < nbk; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
     const int64_t q0 = (int64_t)blockIdx.x * chunk, q1 = min(n, q0 + chunk);
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        int b = slice_bucket(m, __ldg(pose + 3 * q), __ldg(pose + 3 * q + 1), __ldg(pose + 3 * q + 2));
-        bucket[q] = (uint32_t)b;
-        atomicAdd(hist + b, 1u);
+    if (q0 < q1) load_pose_tile(pose, q0, (int)min((int64_t)kSortTile, q1 - q0), reinterpret_cast<float *>(smem));
+    int it = 0;
+    for (int64_t t0 = q0; t0 < q1; t0 += kSortTile, ++it) {
+        const int cnt = (int)min((int64_t)kSortTile, q1 - t0);
+        const int64_t t1 = t0 + kSortTile;
+        if (t1 < q1) {  // the next tile's copies run while this one is counted
+            load_pose_tile(pose, t1, (int)min((int64_t)kSortTile, q1 - t1),
+                           reinterpret_cast<float *>(smem + ((it + 1) & 1) * kPoseBuf));
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float *sp = reinterpret_cast<const float *>(smem + (it & 1) * kPoseBuf);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            int s;
+            bool rev;
+            const int b = sort_bucket(m, sp[3 * i + 2], sh, s, rev);
+            atomicAdd(hist + (b < 0 ? 0 : b), 1u);
+        }
+        __syncthreads();  // this buffer is free for the tile after next
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nbk; b += blockDim.x) counts[(int64_t)b * gridDim.x + blockIdx.x] = hist[b];
 }
 
-__global__ void place_kernel(const uint32_t *bucket, const float *pose, int64_t n, int64_t chunk,
-                             const uint32_t *offsets, int nbk, uint32_t *perm, float *pose_sorted)
+__host__ __device__ constexpr size_t count_smem(int nbk)
 {
-    extern __shared__ uint32_t cursor[];
-    for (int b = threadIdx.x; b < nbk; b += blockDim.x) cursor[b] = offsets[(int64_t)b * gridDim.x + blockIdx.x];
-    __syncthreads();
+    return 2 * (size_t)kPoseBuf + sizeof(uint32_t) * (size_t)nbk;
+}
+
+// Shared memory of sort_place_kernel for nbk buckets: two buffers of
+// kSortTile records (tile i's poses land in buffer i & 1 while tile i - 1 is
+// placed; its records then overwrite them, grouped by bucket), the records'
+// buckets, and per bucket the next output slot, the tile's count and its
+// first tile slot.
+constexpr int kRecBuf = kSortTile * (int)sizeof(uint4);
+__host__ __device__ constexpr size_t place_smem(int nbk)
+{
+    return 2 * (size_t)kRecBuf + (size_t)kSortTile * sizeof(uint16_t) + sizeof(uint32_t) * (3 * (size_t)nbk + 1);
+}
+
+__global__ void __launch_bounds__(kSortThreads, 2) sort_place_kernel(MapView m, const float *pose, int64_t n,
+                                                                     int64_t chunk, int sh, int nbk,
+                                                                     const uint32_t *offsets, uint4 *rec)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    // buffer i & 1 at smem + (i & 1) * kRecBuf: tile i's poses, then its records
+    uint16_t *tbk = reinterpret_cast<uint16_t *>(smem + 2 * kRecBuf);       // the records' buckets
+    uint32_t *cursor = reinterpret_cast<uint32_t *>(tbk + kSortTile);        // next output slot per bucket
+    uint32_t *thist = cursor + nbk;                                          // the tile's queries per bucket
+    uint32_t *toff = thist + nbk;                                            // their first tile slot; [nbk] = total
+    for (int b = threadIdx.x; b < nbk; b += blockDim.x) {
+        cursor[b] = offsets[(int64_t)b * gridDim.x + blockIdx.x];
+        thist[b] = 0;
+    }
     const int64_t q0 = (int64_t)blockIdx.x * chunk, q1 = min(n, q0 + chunk);
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        uint32_t pos = atomicAdd(cursor + bucket[q], 1u);
-        perm[pos] = (uint32_t)q;
-        pose_sorted[3 * (int64_t)pos] = pose[3 * q];
-        pose_sorted[3 * (int64_t)pos + 1] = pose[3 * q + 1];
-        pose_sorted[3 * (int64_t)pos + 2] = pose[3 * q + 2];
+    if (q0 < q1) load_pose_tile(pose, q0, (int)min((int64_t)kSortTile, q1 - q0), reinterpret_cast<float *>(smem));
+    int it = 0;
+    for (int64_t t0 = q0; t0 < q1; t0 += kSortTile, ++it) {
+        const int cnt = (int)min((int64_t)kSortTile, q1 - t0);
+        const int64_t t1 = t0 + kSortTile;
+        if (t1 < q1) {  // the next tile's copies run while this one is placed
+            load_pose_tile(pose, t1, (int)min((int64_t)kSortTile, q1 - t1),
+                           reinterpret_cast<float *>(smem + ((it + 1) & 1) * kRecBuf));
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float *sp = reinterpret_cast<const float *>(smem + (it & 1) * kRecBuf);
+        uint4 *trec = reinterpret_cast<uint4 *>(smem + (it & 1) * kRecBuf);
+        // kSortPerThread queries per thread: buckets and grid cells first,
+        // then every grid read, then the projections and the ranks
+        // (independent reads in flight together)
+        float x[kSortPerThread], y[kSortPerThread];
+        int sl[kSortPerThread], bk[kSortPerThread], rank[kSortPerThread];
+        int64_t cell[kSortPerThread];
+        bool rv[kSortPerThread];
+#pragma unroll
+        for (int j = 0; j < kSortPerThread; ++j) {
+            const int i = j * kSortThreads + threadIdx.x;
+            bk[j] = -1;
+            cell[j] = -1;
+            if (i >= cnt) continue;
+            x[j] = sp[3 * i];
+            y[j] = sp[3 * i + 1];
+            const int b = sort_bucket(m, sp[3 * i + 2], sh, sl[j], rv[j]);
+            bk[j] = b < 0 ? 0 : b;
+            if (b >= 0) cell[j] = map_cell(m.W, m.H, x[j], y[j]);
+        }
+        uint8_t occ[kSortPerThread];
+#pragma unroll
+        for (int j = 0; j < kSortPerThread; ++j) occ[j] = cell[j] >= 0 ? __ldg(m.grid + cell[j]) : 1;
+        uint4 r[kSortPerThread];
+#pragma unroll
+        for (int j = 0; j < kSortPerThread; ++j) {
+            rank[j] = 0;
+            r[j] = make_uint4(__float_as_uint(x[j]), __float_as_uint(y[j]), (uint32_t)(t0 + j * kSortThreads + threadIdx.x),
+                              (uint32_t)sl[j] | (rv[j] ? kRecReverse : 0u) | (occ[j] ? kRecZero : 0u));
+        }
+#pragma unroll
+        for (int j = 0; j < kSortPerThread; ++j)
+            if (bk[j] >= 0) rank[j] = (int)atomicAdd(thist + bk[j], 1u);
+        __syncthreads();  // the poses are read, the tile's counts complete
+        if (threadIdx.x < 32) {  // exclusive scan of the tile's bucket counts
+            const int lane = threadIdx.x, per = (nbk + 31) >> 5, b0 = lane * per;
+            uint32_t sum = 0;
+            for (int i = 0; i < per; ++i)
+                if (b0 + i < nbk) sum += thist[b0 + i];
+            uint32_t inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            uint32_t run = inc - sum;
+            for (int i = 0; i < per; ++i)
+                if (b0 + i < nbk) {
+                    toff[b0 + i] = run;
+                    run += thist[b0 + i];
+                }
+            if (lane == 31) toff[nbk] = inc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortPerThread; ++j)
+            if (bk[j] >= 0) {
+                const int p = (int)toff[bk[j]] + rank[j];
+                trec[p] = r[j];
+                tbk[p] = (uint16_t)bk[j];
+            }
+        __syncthreads();
+        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+            const int b = tbk[p];
+            rec[(size_t)cursor[b] + (size_t)(p - (int)toff[b])] = trec[p];
+        }
+        __syncthreads();  // the records are written out: the buffer and the counts are free
+        for (int b = threadIdx.x; b < nbk; b += blockDim.x) {
+            cursor[b] += thist[b];
+            thist[b] = 0;
+        }
     }
 }
 
+// One thread per record (a stored slice's queries in one direction are
+// consecutive records): the unsorted cast's projection, bin and search.
 template <typename KT, int SEARCH>
-__global__ void calc_range_sorted_kernel(MapView m, const float *pose_sorted, const uint32_t *perm, float *out,
-                                         int64_t n)
+__global__ void __launch_bounds__(256) cast_records_kernel(MapView m, const uint4 *rec, int64_t n, float *out)
 {
-    const uint64_t pol = policy_evict_last();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float x = pose_sorted[3 * i], y = pose_sorted[3 * i + 1], th = pose_sorted[3 * i + 2];
-        out[perm[i]] = cast_one<KT, SEARCH>(m, x, y, th, pol).r;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t pol = policy_evict_normal();
+    const uint4 r = __ldcs(rec + i);
+    float range = 0.0f;
+    if (!(r.w & kRecZero)) {
+        const int s = (int)(r.w & kRecSlice);
+        const float4 sa = __ldg(chk_slice(m, reinterpret_cast<const float4 *>(m.slices + s), 16));
+        float xr, yr;
+        project(__uint_as_float(r.x), __uint_as_float(r.y), sa.x, sa.y, xr, yr);
+        const uint32_t Tnb = __float_as_uint(sa.w);
+        const int b = query_bin(yr, (int)(Tnb & 0xffffu));
+        range = m.max_range;
+        if (b >= 0 && b < (int)(Tnb >> 16)) {
+            const uint32_t g = __float_as_uint(sa.z) + (uint32_t)b;
+            const float X = sizeof(KT) == 4 ? 0.0f : __ldg(chk_slice(m, &m.slices[s].X, 4));
+            int kb;
+            if (!(r.w & kRecReverse)) {  // forward: first key > x'
+                const SearchResult sr = bin_search<KT, true, SEARCH>(m, g, xr, X, pol, kb);
+                if (sr.idx < kb) {
+                    const float d = __fsub_rn(sr.at, xr);
+                    if (d < m.max_range) range = d;
+                }
+            } else {  // reverse: last key < x'
+                const SearchResult sr = bin_search<KT, false, SEARCH>(m, g, xr, X, pol, kb);
+                if (sr.idx > 0) {
+                    const float d = __fsub_rn(xr, sr.prev);
+                    if (d < m.max_range) range = d;
+                }
+            }
+        }
     }
+    out[r.z] = range;
 }
 
 // ------------------------------------------------------------ host
@@ -165,32 +377,103 @@ cddt_status launch_sensor(const cddt_s *h, const SensorArgs &a, int mode, cudaSt
     return h->u16 ? launch_sensor_u16(h, a, mode, tpp, 256, st) : launch_sensor_f32(h, a, mode, tpp, 256, st);
 }
 
+// Shape of the slice sort for n queries.
+struct SortShape {
+    int sh, nbk;                   // bucket = slice >> sh, nbk buckets
+    int64_t nblk, chunk, ncount;   // blocks, queries per block, (bucket, block) counts
+};
+
+// Blocks of the count and place passes that fit on one streaming
+// multiprocessor at once (both passes use the same blocks).
+static int sort_blocks_per_sm(int nbk)
+{
+    int a = 0, b = 0;
+    if (cudaFuncSetAttribute(sort_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)count_smem(kMaxSortBuckets)) != cudaSuccess ||
+        cudaFuncSetAttribute(sort_place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)place_smem(kMaxSortBuckets)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sort_count_kernel, kSortThreads, count_smem(nbk)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sort_place_kernel, kSortThreads, place_smem(nbk)) !=
+            cudaSuccess)
+        return 1;
+    return std::max(1, std::min(a, b));
+}
+
+static SortShape sort_shape(const cddt_s *h, int64_t n)
+{
+    SortShape p;
+    p.sh = 0;
+    while (((2 * h->S - 1) >> p.sh) + 1 > kMaxSortBuckets) ++p.sh;
+    p.nbk = ((2 * h->S - 1) >> p.sh) + 1;
+    // one wave of blocks, each a whole number of tiles
+    const int64_t nn = std::max<int64_t>(n, 1);
+    const int64_t waves = (int64_t)sm_count() * sort_blocks_per_sm(p.nbk);
+    const int64_t tiles = (nn + kSortTile - 1) / kSortTile;
+    p.chunk = ((tiles + waves - 1) / waves) * kSortTile;
+    p.nblk = (nn + p.chunk - 1) / p.chunk;
+    p.ncount = (int64_t)p.nbk * p.nblk;
+    return p;
+}
+
+// Scratch of the sort: scan partials and total | (bucket, block) counts |
+// 16-byte aligned records, one per query.
+static int64_t sort_scratch_bytes(const SortShape &p, int64_t n)
+{
+    return 8 * (scan_scratch_elems(p.ncount) + 2) + 4 * p.ncount + 16 + 16 * n;
+}
+
+int64_t sorted_scratch_bytes(const cddt_s *h, int64_t n) { return sort_scratch_bytes(sort_shape(h, n), n); }
+
+cddt_status calc_range_sorted_into(cddt_s *h, const float *pose, float *out, int64_t n, void *scratch,
+                                   int64_t scratch_bytes, cudaStream_t st)
+{
+    if (n == 0) return CDDT_OK;
+    if (n > 0xffffffffll) return CDDT_ERR_ARG;
+    const SortShape p = sort_shape(h, n);
+    if (sort_scratch_bytes(p, n) > scratch_bytes) return CDDT_ERR_ARG;
+    char *c = reinterpret_cast<char *>(scratch);
+    uint64_t *scan_part = reinterpret_cast<uint64_t *>(c);
+    uint64_t *total = scan_part + scan_scratch_elems(p.ncount);
+    c += 8 * (scan_scratch_elems(p.ncount) + 2);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(c);
+    c += 4 * p.ncount;
+    uint4 *rec = reinterpret_cast<uint4 *>(((uintptr_t)c + 15) & ~(uintptr_t)15);
+    const MapView m = h->view();
+    // (sort_shape set both kernels' shared-memory limits)
+    sort_count_kernel<<<(unsigned)p.nblk, kSortThreads, count_smem(p.nbk), st>>>(m, pose, n, p.chunk, p.sh, p.nbk,
+                                                                                 counts);
+    exclusive_scan_u32(counts, counts, p.ncount, scan_part, total, st);
+    sort_place_kernel<<<(unsigned)p.nblk, kSortThreads, place_smem(p.nbk), st>>>(m, pose, n, p.chunk, p.sh, p.nbk,
+                                                                                 counts, rec);
+    const bool bin = h->search == CDDT_SEARCH_BINARY;
+    const int64_t blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffff) return CDDT_ERR_ARG;
+    const unsigned g = (unsigned)blocks;
+    if (h->u16 && bin) cast_records_kernel<uint16_t, CDDT_SEARCH_BINARY><<<g, 256, 0, st>>>(m, rec, n, out);
+    else if (h->u16) cast_records_kernel<uint16_t, CDDT_SEARCH_TREE><<<g, 256, 0, st>>>(m, rec, n, out);
+    else if (bin) cast_records_kernel<float, CDDT_SEARCH_BINARY><<<g, 256, 0, st>>>(m, rec, n, out);
+    else cast_records_kernel<float, CDDT_SEARCH_TREE><<<g, 256, 0, st>>>(m, rec, n, out);
+    CDDT_CUDA(cudaGetLastError());
+    return CDDT_OK;
+}
+
 cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int sorted, cudaStream_t st)
 {
     if (n == 0) return CDDT_OK;
-    MapView m = h->view();
-    const int threads = 256;
     if (!sorted) {
-        unsigned blocks = grid_cap(n, threads, 152 * 64);
+        const MapView m = h->view();
+        const unsigned blocks = grid_cap(n, 256, 64);
         const bool bin = h->search == CDDT_SEARCH_BINARY;
-        if (h->u16 && bin) calc_range_kernel<uint16_t, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose, out, n);
-        else if (h->u16) calc_range_kernel<uint16_t, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose, out, n);
-        else if (bin) calc_range_kernel<float, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose, out, n);
-        else calc_range_kernel<float, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose, out, n);
+        if (h->u16 && bin) calc_range_kernel<uint16_t, CDDT_SEARCH_BINARY><<<blocks, 256, 0, st>>>(m, pose, out, n);
+        else if (h->u16) calc_range_kernel<uint16_t, CDDT_SEARCH_TREE><<<blocks, 256, 0, st>>>(m, pose, out, n);
+        else if (bin) calc_range_kernel<float, CDDT_SEARCH_BINARY><<<blocks, 256, 0, st>>>(m, pose, out, n);
+        else calc_range_kernel<float, CDDT_SEARCH_TREE><<<blocks, 256, 0, st>>>(m, pose, out, n);
         CDDT_CUDA(cudaGetLastError());
         return CDDT_OK;
     }
     if (n > 0xffffffffll) return CDDT_ERR_ARG;
-    const int nbk = h->S + 1;
-    if ((size_t)nbk * sizeof(uint32_t) > 200 * 1024) return CDDT_ERR_ARG;
-    int nsm = 0;
-    CDDT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    int64_t nblk = std::min<int64_t>((int64_t)nsm * 4, (n + kSortThreads - 1) / kSortThreads);
-    const int64_t chunk = (n + nblk - 1) / nblk;
-    nblk = (n + chunk - 1) / chunk;
-    const int64_t ncount = (int64_t)nbk * nblk;
-    // scratch: scan scratch | counts/offsets | bucket[n] | perm[n] | sorted poses[3n]
-    int64_t need = 8 * (scan_scratch_elems(ncount) + 2) + 4 * ncount + 4 * n + 4 * n + 12 * n + 256;
+    const int64_t need = sorted_scratch_bytes(h, n);
     if (need > h->qscratch_bytes) {
         CDDT_CUDA(cudaStreamSynchronize(st));
         if (h->qscratch) cudaFree(h->qscratch);
@@ -199,90 +482,9 @@ cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int 
         CDDT_CUDA(cudaMalloc(&h->qscratch, (size_t)need));
         h->qscratch_bytes = need;
     }
-    char *p = reinterpret_cast<char *>(h->qscratch);
-    uint64_t *scan_scratch = reinterpret_cast<uint64_t *>(p);
-    p += 8 * (scan_scratch_elems(ncount) + 2);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(p);
-    p += 4 * ncount;
-    p = reinterpret_cast<char *>(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    uint32_t *bucket = reinterpret_cast<uint32_t *>(p);
-    p += 4 * n;
-    uint32_t *perm = reinterpret_cast<uint32_t *>(p);
-    p += 4 * n;
-    float *pose_sorted = reinterpret_cast<float *>(p);
-    const size_t hs = sizeof(uint32_t) * nbk;
-    if (hs > 48 * 1024) {
-        CDDT_CUDA(cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs));
-        CDDT_CUDA(cudaFuncSetAttribute(place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs));
-    }
-    bucket_count_kernel<<<(unsigned)nblk, kSortThreads, hs, st>>>(m, pose, n, chunk, bucket, counts, nbk);
-    exclusive_scan_u32(counts, counts, ncount, scan_scratch, scan_scratch + scan_scratch_elems(ncount), st);
-    place_kernel<<<(unsigned)nblk, kSortThreads, hs, st>>>(bucket, pose, n, chunk, counts, nbk, perm, pose_sorted);
-    unsigned blocks = grid_cap(n, threads, 152 * 64);
-    const bool bin = h->search == CDDT_SEARCH_BINARY;
-    if (h->u16 && bin) calc_range_sorted_kernel<uint16_t, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    else if (h->u16) calc_range_sorted_kernel<uint16_t, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    else if (bin) calc_range_sorted_kernel<float, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    else calc_range_sorted_kernel<float, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    CDDT_CUDA(cudaGetLastError());
-    return CDDT_OK;
+    return calc_range_sorted_into(h, pose, out, n, h->qscratch, h->qscratch_bytes, st);
 }
 
-// Slice-sorted ray casting on caller-provided scratch (no allocation).  The
-// scratch layout is that of calc_range's sorted path; sorted_scratch_bytes
-// gives its size for n queries.
-int64_t sorted_scratch_bytes(const cddt_s *h, int64_t n)
-{
-    const int nbk = h->S + 1;
-    int nsm = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) return -1;
-    int64_t nblk = std::min<int64_t>((int64_t)nsm * 4, (n + kSortThreads - 1) / kSortThreads);
-    if (nblk < 1) nblk = 1;
-    const int64_t chunk = (n + nblk - 1) / nblk;
-    nblk = std::max<int64_t>((n + chunk - 1) / std::max<int64_t>(chunk, 1), 1);
-    const int64_t ncount = (int64_t)nbk * nblk;
-    return 8 * (scan_scratch_elems(ncount) + 2) + 4 * ncount + 16 + 4 * n + 4 * n + 12 * n;
-}
-
-cddt_status calc_range_sorted_into(cddt_s *h, const float *pose, float *out, int64_t n, void *scratch,
-                                   int64_t scratch_bytes, cudaStream_t st)
-{
-    if (n == 0) return CDDT_OK;
-    MapView m = h->view();
-    const int threads = 256;
-    const int nbk = h->S + 1;
-    const size_t hs = sizeof(uint32_t) * nbk;
-    if (hs > 48 * 1024) return CDDT_ERR_ARG;
-    int nsm = 0;
-    CDDT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    int64_t nblk = std::min<int64_t>((int64_t)nsm * 4, (n + kSortThreads - 1) / kSortThreads);
-    const int64_t chunk = (n + nblk - 1) / nblk;
-    nblk = (n + chunk - 1) / chunk;
-    const int64_t ncount = (int64_t)nbk * nblk;
-    if (sorted_scratch_bytes(h, n) > scratch_bytes) return CDDT_ERR_ARG;
-    char *p = reinterpret_cast<char *>(scratch);
-    uint64_t *scan_scratch = reinterpret_cast<uint64_t *>(p);
-    p += 8 * (scan_scratch_elems(ncount) + 2);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(p);
-    p += 4 * ncount;
-    p = reinterpret_cast<char *>(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    uint32_t *bucket = reinterpret_cast<uint32_t *>(p);
-    p += 4 * n;
-    uint32_t *perm = reinterpret_cast<uint32_t *>(p);
-    p += 4 * n;
-    float *pose_sorted = reinterpret_cast<float *>(p);
-    bucket_count_kernel<<<(unsigned)nblk, kSortThreads, hs, st>>>(m, pose, n, chunk, bucket, counts, nbk);
-    exclusive_scan_u32(counts, counts, ncount, scan_scratch, scan_scratch + scan_scratch_elems(ncount), st);
-    place_kernel<<<(unsigned)nblk, kSortThreads, hs, st>>>(bucket, pose, n, chunk, counts, nbk, perm, pose_sorted);
-    const unsigned blocks = grid_cap(n, threads, 152 * 64);
-    const bool bin = h->search == CDDT_SEARCH_BINARY;
-    if (h->u16 && bin) calc_range_sorted_kernel<uint16_t, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    else if (h->u16) calc_range_sorted_kernel<uint16_t, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    else if (bin) calc_range_sorted_kernel<float, CDDT_SEARCH_BINARY><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    else calc_range_sorted_kernel<float, CDDT_SEARCH_TREE><<<blocks, threads, 0, st>>>(m, pose_sorted, perm, out, n);
-    CDDT_CUDA(cudaGetLastError());
-    return CDDT_OK;
-}
 
 // ------------------------------------------------------------ plans
 

@@ -219,7 +219,7 @@ cddt_status cddt_rm_calc_range_many(cddt_rm R, const float *pose_dev, float *ran
     if (!R || n < 0 || (n > 0 && (!pose_dev || !range_dev))) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_rm_calc_range_many");
     if (n == 0) return CDDT_OK;
-    cddt::rm_kernel<<<cddt::grid_cap(n, 256, 152 * 64), 256, 0, (cudaStream_t)stream>>>(
+    cddt::rm_kernel<<<cddt::grid_cap(n, 256, 64), 256, 0, (cudaStream_t)stream>>>(
         R->dist, R->W, R->H, pose_dev, range_dev, steps_dev, n, R->max_range);
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;

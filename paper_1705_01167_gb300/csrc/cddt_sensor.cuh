@@ -318,7 +318,7 @@ inline cddt_status launch_sensor_tpp(const cddt_s *h, const SensorArgs &a, int t
     MapView m = h->view();
     int ppb = threads / tpp;
     int64_t blocks = (a.P + ppb - 1) / ppb;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
     if (blocks < 1) blocks = 1;
     size_t sm = beam_smem(a.B);
     void (*fn)(MapView, SensorArgs) = nullptr;
