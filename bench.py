@@ -13,7 +13,13 @@ on the pruned CDDT and on the 16-bit store, with uniform particles, as a
 full filter step (motion, sensor model, resampling), end to end from
 page-locked host buffers, a 10 M-query random and a 50 M-state grid sweep
 with per-warp latency, the paper's comparison casters (lookup table, ray
-marching, Bresenham) on both samples (`methods`), and the CPU oracle.
+marching, Bresenham) on both samples (`methods`), one filter step of the
+paper's one-robot setting through the C ABI (`single_filter_step`), the CPU
+oracle, and compact measurements of the other four configurations
+(`configs`: rects256, batched64, diff2000, update4000; skip with
+--no-configs).  `roofline.binding` states the fused kernel's fraction of the
+limit that binds it (the L1 data pipe), from ncu's wavefront count on the
+current kernel source.
 `clocks` summarises timestamped nvidia-smi samples (every 200 ms, or
 CDDT_CLOCKS_MS; raw samples kept in CDDT_CLOCKS_DIR when set) over the
 timed region, or the nearest ones when the region is shorter than the
@@ -24,7 +30,8 @@ Other workloads (same JSON line, `config.name` names them):
   batched64     64 maps 512^2..4096^2, theta_disc 100..360, 500..10000
                 particles each: one persistent launch vs 64 per-filter launches
   diff2000      forward + adjoint, 4096 x 61 and 1024 x 1081 beams, with 10
-                gradient refinement steps
+                gradient refinement steps, in one launch (cddt_plan_refine),
+                beside the step-by-step loop
   update4000    4000 x 4000, theta_disc 360: 10^4 cell writes through
                 cddt_update_cells, then 100,000 particles x 61 beams
 
@@ -65,8 +72,8 @@ WORKLOAD_TEXT = {
     "rects256": "rectangles 256x256 (~17% occupied), theta_disc 108, max range 300; 1000 particles x 61 beams",
     "batched64": ("64 corridor maps 512^2..4096^2, theta_disc 100..360, 500..10000 particles x 61 beams each; "
                   "one persistent launch"),
-    "diff2000": ("corridor 2000x2000, theta_disc 200; forward + adjoint for 4096 x 61 and 1024 x 1081 beams, "
-                 "plus 10 gradient refinement steps"),
+    "diff2000": ("corridor 2000x2000, theta_disc 200; forward + adjoint for 4096 x 61 and 1024 x 1081 beams "
+                 "with 10 gradient refinement steps (11 evaluations), one launch"),
     "update4000": ("corridor 4000x4000, theta_disc 360, max range 1000; 10^4 cell writes per step through "
                    "cddt_update_cells, then 100,000 particles x 61 beams"),
 }
@@ -164,7 +171,10 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "batched_kernel": ("cddt_internal.cuh", "cddt_sensor.cuh", "cddt_batched_f32.cu"),
     "calc_range_kernel": ("cddt_internal.cuh", "cddt_query.cu"),
+    "refine_kernel": ("cddt_internal.cuh", "cddt_sensor.cuh", "cddt_refine.cu"),
 }
+# recorded workloads of the same kernel (another launch shape or input)
+KERNEL_OF = {"batched_kernel_uniform": "batched_kernel"}
 
 
 def kernel_source_sha(kernel: str) -> str:
@@ -175,16 +185,23 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, launch_units: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this
-    launch's units, when it was taken on the current kernel source."""
+def recorded(kernel: str):
+    """The committed ncu counts of a profiled kernel (profiles/traffic.json),
+    when they were taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
-    if not d or d.get("source_sha") != kernel_source_sha(kernel):
+    if not d or d.get("source_sha") != kernel_source_sha(KERNEL_OF.get(kernel, kernel)):
         return None
-    return d["dram_bytes_per_unit"] * launch_units
+    return d
+
+
+def recorded_traffic(kernel: str, launch_units: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    launch's units, when it was taken on the current kernel source."""
+    d = recorded(kernel)
+    return None if d is None else d["dram_bytes_per_unit"] * launch_units
 
 
 def algorithmic_bytes(work: dict, P: int) -> int:
@@ -459,6 +476,21 @@ def bench_corridor(args, G, torch, dev, world, rank):
     ms_u = timed(plan_u.run, k2, 2)
     extra["uniform_particles_rays_per_s"] = rays_per_step / (statistics.mean(ms_u) * 1e-3)
     extra["uniform_particles_shape"] = shape_u
+    # its roofline: algorithmic bytes over the same HBM copy peak, and the
+    # DRAM bytes ncu counted per particle (its gathers leave the caches)
+    work_u = {}
+    for t in range(S):
+        add_work(work_u, d.sensor_work(upart_d[t * P:(t + 1) * P], bo_d, D))
+    alg_u = algorithmic_bytes(work_u, S * P)
+    mean_s = statistics.mean(ms_u) * 1e-3
+    rec_u = recorded("batched_kernel_uniform")
+    dram_u = None if rec_u is None else rec_u["dram_bytes_per_unit"] * S * P
+    extra["uniform_particles_roofline"] = {
+        "bound": "hbm", "achieved": alg_u / mean_s / 1e9, "peak": peak, "unit": "GB/s",
+        "frac": alg_u / mean_s / 1e9 / peak, "traffic": dram_u, "peak_kind": peak_kind,
+        "algorithmic_bytes_per_launch": alg_u, "sector_bytes_per_launch": sector_bytes(work_u, S * P),
+        "dram_gbs": None if dram_u is None else dram_u / mean_s / 1e9,
+        "dram_frac": None if dram_u is None else dram_u / mean_s / 1e9 / peak}
     plan_u.close()
 
     def sequential():
@@ -467,6 +499,56 @@ def bench_corridor(args, G, torch, dev, world, rank):
     ms_s = timed(sequential, k2, 2)
     extra["sequential_rays_per_s"] = rays_per_step / (statistics.mean(ms_s) * 1e-3)
     extra["batched_speedup_vs_sequential"] = statistics.mean(ms_s) / statistics.mean(ms)
+
+    # one filter step of the paper's one-robot setting (Section VI: 2500
+    # particles x 61 beams, 40 Hz on one CPU thread there), through the C ABI:
+    # a one-filter plan launched as a CUDA graph (device time per step), the
+    # same with the motion model and resampling in the graph, and the wall
+    # time of one cddt_sensor_weights call from the host to its completion
+    f0 = filters_for(d)[0]
+    plan1 = G.Plan([f0])
+    shape1 = plan1.autotune()
+    ms1 = timed(plan1.launch_graph, 50, 5)
+    seg1 = torch.tensor([0, P], dtype=torch.int64, device=dev)
+    odo1, u01 = odom_d[:1].contiguous(), u0_d[:1].contiguous()
+    src1 = parts_d[:P].clone()
+    dst1 = torch.empty_like(src1)
+    noise1 = torch.from_numpy((rs_m.normal(3 * P) * 0.05).astype(np.float32).reshape(-1, 3)).to(dev)
+    scr1 = torch.empty(P, dtype=torch.float64, device=dev)
+    plan1m = G.Plan([dict(f0, particles=src1)])
+    plan1m.set_shape(**shape1)
+
+    def step1():
+        G.motion(src1, seg1, odo1, noise1)
+        plan1m.run()
+        G.resample(src1, f0["logw"], seg1, u01, out=dst1, scratch=scr1)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step1()
+    torch.cuda.current_stream().wait_stream(side)
+    gr1 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr1):
+        step1()
+    ms1m = timed(gr1.replay, 50, 5)
+    for _ in range(20):
+        d.sensor_weights(f0["particles"], bo_d, f0["obs"], m, D, logw=f0["logw"])
+    torch.cuda.synchronize()
+    n_calls = 200
+    t0 = time.perf_counter()
+    for _ in range(n_calls):
+        d.sensor_weights(f0["particles"], bo_d, f0["obs"], m, D, logw=f0["logw"])
+        torch.cuda.synchronize()
+    call_us = (time.perf_counter() - t0) / n_calls * 1e6
+    extra["single_filter_step"] = {
+        "particles": P, "beams": B, "sensor_graph_us": statistics.mean(ms1) * 1e3,
+        "mcl_step_graph_us": statistics.mean(ms1m) * 1e3, "sensor_call_wall_us": call_us,
+        "shape": shape1, "steps_per_s_graph": 1e3 / statistics.mean(ms1),
+        "note": "device time per CUDA-graph launch (L2 flushed before each); the call's wall time includes "
+                "the Python binding, the C-ABI argument checks, the launch and a stream synchronize"}
+    plan1.close()
+    plan1m.close()
+    del src1, dst1, noise1, scr1
 
     d.set_search(G.SEARCH_BINARY)
     ms_b = timed(plan.run, k2, 2)
@@ -626,6 +708,27 @@ def bench_corridor(args, G, torch, dev, world, rank):
     e2e_ms = max_over_ranks(world, statistics.mean(ms_e))
     plan_h.close()
 
+    # the limit that binds the tracking workload: the L1 data pipe, one
+    # wavefront per cycle per SM (global and shared wavefronts counted by ncu
+    # on this kernel source), at the SM clock sampled in the timed region
+    rec = recorded("batched_kernel")
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    wf_peak = nsm * sm_mhz * 1e6 / 1e9  # G wavefronts/s
+    if rec and rec.get("l1_wavefronts_per_unit"):
+        wf = rec["l1_wavefronts_per_unit"] * S * P
+        binding = {"limit": "l1_data_pipe", "achieved": wf / (ms_step * 1e-3) / 1e9, "peak": wf_peak,
+                   "unit": "G wavefronts/s", "frac": wf / (ms_step * 1e-3) / 1e9 / wf_peak,
+                   "wavefronts_per_particle": rec["l1_wavefronts_per_unit"], "sms": nsm, "sm_mhz": sm_mhz,
+                   "source": "ncu l1tex__data_pipe_lsu_wavefronts_mem_lg + _mem_shared per launch, this kernel source"}
+    else:
+        binding = {"limit": "l1_data_pipe", "achieved": None, "peak": wf_peak, "unit": "G wavefronts/s",
+                   "frac": None, "sms": nsm, "sm_mhz": sm_mhz,
+                   "source": "no ncu wavefront count recorded for this kernel source"}
+    configs = {}
+    if not args.no_configs:
+        for name, fn in MEASURES.items():
+            configs[name] = fn(G, torch, dev, world, rank, args.config_steps, 3)
     line = base_line(args, world, value, ms_step, "corridor2000",
                      {"launch": f"persistent batched, autotuned {shape}", "zero_points": st0["n_zero_points"],
                       "store_bytes": st0["store_bytes"], "occupancy": round(synth.occupancy(w["grid"]), 4)})
@@ -636,16 +739,17 @@ def bench_corridor(args, G, torch, dev, world, rank):
                      "sector_bytes_per_launch": sec, "sector_gbs": sec / (ms_step * 1e-3) / 1e9,
                      "gather_gbs_measured": gbw,
                      "sector_frac_of_hbm_gather": sec / (ms_step * 1e-3) / 1e9 / gbw["hbm"],
-                     "limiter": ("on-chip: L1 data-pipe wavefronts and instruction issue (ncu, "
-                                 "profiles/batched_kernel_corridor2000.md); the tracking filter's "
-                                 "gathers are cache resident, DRAM traffic ~1 % of the algorithmic bytes")},
+                     "binding": binding,
+                     "limiter": ("on-chip: the L1 data pipe (wavefronts, binding.frac) and instruction issue (ncu "
+                                 "capture of batched_kernel on this workload); the tracking filter's gathers are "
+                                 "cache resident, DRAM traffic ~1 % of the algorithmic bytes")},
         "e2e": {"value": world * rays_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(parts_h.numel() * 4 + obs_h.numel() * 4),
                 "d2h_bytes_per_step": int(logw_h.numel() * 4),
                 "path": "plan on page-locked host buffers (kernel reads and writes them across the host link)",
                 "copy_engine_value": world * rays_per_step / (copy_ms * 1e-3)},
         "gpu_launches": args.steps, "clocks": clocks,
-        "build_ms": st0["build_ms"], "build_wall_s": build_wall, **extra})
+        "build_ms": st0["build_ms"], "build_wall_s": build_wall, **extra, "configs": configs})
     if not args.no_cpu and rank == 0 and world == 1:
         from oracle import oracle as O
         cores = os.cpu_count() or 1
@@ -663,7 +767,17 @@ def bench_corridor(args, G, torch, dev, world, rank):
     return line
 
 
-def bench_rects(args, G, torch, dev, world, rank):
+# ------------------------------------------------------------------ the other configurations
+#
+# Each measure_* function times one configuration and returns a compact dict
+# (rays/s and the figures the configuration is about); the default line
+# carries all four under "configs", and `--workload NAME` prints one as its
+# own line.
+
+def measure_rects(G, torch, dev, world, rank, steps, warmup):
+    """rects256: one 1000-particle filter, one cddt_sensor_weights call per
+    step (host call + launch), and the same as a one-filter plan under a CUDA
+    graph."""
     w = WL.rects256()
     bo, D, mr = w["beam_off"], w["D"], w["max_range"]
     d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], mr)
@@ -674,22 +788,25 @@ def bench_rects(args, G, torch, dev, world, rank):
     logw = torch.empty(parts.shape[0], device=dev)
     m = G.beam_model(mr)
     timed = Timer(world, dev)
-    ms = timed(lambda: d.sensor_weights(parts, bo_d, obs, m, D, logw=logw), args.steps, args.warmup)
+    with ClockSampler(dev.index) as clk:
+        ms = timed(lambda: d.sensor_weights(parts, bo_d, obs, m, D, logw=logw), steps, warmup)
     ms_step = max_over_ranks(world, statistics.mean(ms))
     rays = parts.shape[0] * bo.size
     plan = G.Plan([dict(map=d, particles=parts, beam_off=bo_d, obs=obs, model=m, logw=logw, pair_offset=D)])
     plan.autotune()
-    ms_g = timed(plan.launch_graph, args.steps, 2)
+    ms_g = timed(plan.launch_graph, steps, 2)
     st = d.stats()
-    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "rects256",
-                     {"launch": "cddt_sensor_weights, one launch per step"})
-    line.update({"gpu_launches": args.steps, "graph_rays_per_s": rays / (statistics.mean(ms_g) * 1e-3),
-                 "build_ms": st["build_ms"], "zero_points": st["n_zero_points"]})
     plan.close()
-    return line
+    d.close()
+    return {"rays_per_s": world * rays / (ms_step * 1e-3), "ms_per_step": ms_step, "rays_per_step": rays,
+            "graph_rays_per_s": rays / (statistics.mean(ms_g) * 1e-3), "build_ms": st["build_ms"],
+            "zero_points": st["n_zero_points"], "clocks": clk.summary(timed.window),
+            "launch": "cddt_sensor_weights, one call per step"}
 
 
-def bench_batched64(args, G, torch, dev, world, rank):
+def measure_batched64(G, torch, dev, world, rank, steps, warmup):
+    """batched64: 64 maps and filters in one persistent launch under a CUDA
+    graph, against the same filters as 64 per-filter launches."""
     w = WL.batched64(seed_offset=RK.seed_offset(rank))
     bo = torch.from_numpy(w["beam_off"]).to(dev)
     D = w["D"]
@@ -707,76 +824,90 @@ def bench_batched64(args, G, torch, dev, world, rank):
     timed = Timer(world, dev)
     rays = sum(f["particles"].shape[0] for f in filters) * bo.numel()
     with ClockSampler(dev.index) as clk:
-        ms = timed(plan.launch_graph, args.steps, args.warmup)
-    clock_window = timed.window
+        ms = timed(plan.launch_graph, steps, warmup)
+    clocks = clk.summary(timed.window)
     ms_step = max_over_ranks(world, statistics.mean(ms))
 
     def sequential():
         for f in filters:
             f["map"].sensor_weights(f["particles"], bo, f["obs"], f["model"], D, logw=f["logw"])
-    ms_s = timed(sequential, max(3, args.steps // 2), 2)
-    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "batched64",
-                     {"launch": f"persistent batched under a CUDA graph, autotuned {shape}",
-                      "particles": rays // bo.numel()})
-    line.update({"gpu_launches": args.steps, "clocks": clk.summary(clock_window),
-                 "sequential_rays_per_s": rays / (statistics.mean(ms_s) * 1e-3),
-                 "batched_speedup_vs_sequential": statistics.mean(ms_s) / statistics.mean(ms),
-                 "build_ms_total": sum(build_ms)})
+    ms_s = timed(sequential, max(3, steps // 2), 2)
     plan.close()
-    return line
+    for f in filters:
+        f["map"].close()
+    return {"rays_per_s": world * rays / (ms_step * 1e-3), "ms_per_step": ms_step, "rays_per_step": rays,
+            "particles": rays // bo.numel(), "sequential_rays_per_s": rays / (statistics.mean(ms_s) * 1e-3),
+            "batched_speedup_vs_sequential": statistics.mean(ms_s) / statistics.mean(ms),
+            "build_ms_total": sum(build_ms), "shape": shape, "clocks": clocks,
+            "launch": "persistent batched under a CUDA graph vs 64 cddt_sensor_weights launches"}
 
 
-def bench_diff(args, G, torch, dev, world, rank):
+def measure_diff(G, torch, dev, world, rank, steps, warmup):
+    """diff2000: forward + adjoint of 4096 x 61 and 1024 x 1081 beams with 10
+    gradient refinement steps x += eta g / |g| (11 evaluations): in one
+    launch (cddt_plan_refine), and as the step-by-step loop of
+    cddt_sensor_weights_fwd_bwd calls and torch updates, eager and captured
+    in a CUDA graph; the forward pass alone beside them."""
     w = WL.diff2000(seed_offset=RK.seed_offset(rank))
     mr = w["max_range"]
     d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], mr)
     m = G.beam_model(mr)
-    scans = []
+    scans, filters = [], []
     for sc in w["scans"]:
         r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], sc["beam_off"])).to(dev)).cpu().numpy()
         obs = torch.from_numpy(np.clip(r + sc["noise"], 0, mr).astype(np.float32)).to(dev)
-        scans.append((torch.from_numpy(sc["parts"]).to(dev), torch.from_numpy(sc["beam_off"]).to(dev), obs, sc["D"]))
+        p0, bo = torch.from_numpy(sc["parts"]).to(dev), torch.from_numpy(sc["beam_off"]).to(dev)
+        P = p0.shape[0]
+        scans.append((p0, bo, obs, sc["D"]))
+        filters.append(dict(map=d, particles=p0, beam_off=bo, obs=obs, model=m, logw=torch.empty(P, device=dev),
+                            pair_offset=sc["D"], grad_xy=torch.empty((P, 2), device=dev),
+                            particles_out=torch.empty((P, 3), device=dev)))
+    n_eval = w["refine_steps"] + 1
+    rays_eval = sum(p.shape[0] * bo.numel() for p, bo, _, _ in scans)
+    rays = rays_eval * n_eval
+    plan = G.Plan(filters)
     timed = Timer(world, dev)
+    with ClockSampler(dev.index) as clk:
+        ms = timed(lambda: plan.refine(w["refine_steps"], w["eta"]), steps, warmup)
+    clocks = clk.summary(timed.window)
+    ms_step = max_over_ranks(world, statistics.mean(ms))
 
-    def step():  # forward + adjoint, then 10 refinement steps, for both scans
+    def loop():  # forward + adjoint, then the update, n_eval times per scan
         for p0, bo, obs, D in scans:
             x = p0.clone()
-            for _ in range(w["refine_steps"] + 1):
+            for _ in range(n_eval):
                 lw, g = d.sensor_weights_fwd_bwd(x, bo, obs, m, D)
                 n = torch.linalg.norm(g, dim=1, keepdim=True).clamp_min(1e-12)
                 x[:, :2] += w["eta"] * g / n
-    ms = timed(step, args.steps, args.warmup)
-    ms_step = max_over_ranks(world, statistics.mean(ms))
-    rays = sum(p.shape[0] * bo.numel() for p, bo, _, _ in scans) * (w["refine_steps"] + 1)
-    fwd = timed(lambda: [d.sensor_weights(p, bo, obs, m, D) for p, bo, obs, D in scans], args.steps, 2)
-    rays_fwd = sum(p.shape[0] * bo.numel() for p, bo, _, _ in scans)
-    # the same step captured once in a CUDA graph (the library's calls are
-    # stream-ordered and allocate nothing), replayed
+    ms_e = timed(loop, max(3, steps // 2), 2)
     graph_rays = None
     try:
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
-            step()
+            loop()
         torch.cuda.current_stream().wait_stream(side)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
-            step()
-        ms_g = timed(graph.replay, args.steps, 2)
-        graph_rays = rays / (statistics.mean(ms_g) * 1e-3)
+            loop()
+        graph_rays = rays / (statistics.mean(timed(graph.replay, max(3, steps // 2), 2)) * 1e-3)
     except RuntimeError as e:
-        print(f"graph capture of the refinement step failed: {e}", file=sys.stderr)
-    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "diff2000",
-                     {"launch": "cddt_sensor_weights_fwd_bwd per refinement step (value counts forward+adjoint "
-                                "ray casts)"})
-    line.update({"gpu_launches": args.steps * 2 * (w["refine_steps"] + 1),
-                 "forward_only_rays_per_s": rays_fwd / (statistics.mean(fwd) * 1e-3),
-                 "graph_rays_per_s": graph_rays})
-    return line
+        print(f"graph capture of the refinement loop failed: {e}", file=sys.stderr)
+    fwd = timed(lambda: [d.sensor_weights(p, bo, obs, m, D) for p, bo, obs, D in scans], max(3, steps // 2), 2)
+    plan.close()
+    d.close()
+    return {"rays_per_s": world * rays / (ms_step * 1e-3), "ms_per_step": ms_step, "rays_per_step": rays,
+            "launch": "cddt_plan_refine: 10 refinement steps + final evaluation, one launch (value counts "
+                      "forward+adjoint ray casts)",
+            "loop_rays_per_s": rays / (statistics.mean(ms_e) * 1e-3), "loop_graph_rays_per_s": graph_rays,
+            "forward_only_rays_per_s": rays_eval / (statistics.mean(fwd) * 1e-3), "clocks": clocks}
 
 
-def bench_update(args, G, torch, dev, world, rank):
-    w = WL.update4000(steps=args.steps + args.warmup, seed_offset=RK.seed_offset(rank))
+def measure_update(G, torch, dev, world, rank, steps, warmup):
+    """update4000: 10^4 cell writes (5000 inserts, 5000 removes) through
+    cddt_update_cells on a 4000 x 4000 map (theta_disc 360), then 100,000
+    particles x 61 beams; full build and prune (on a separate handle) times."""
+    w = WL.update4000(steps=steps + warmup, seed_offset=RK.seed_offset(rank))
     mr = w["max_range"]
     grid = torch.from_numpy(w["grid"]).to(dev)
     d = G.CDDT(grid, w["theta_disc"], mr)
@@ -800,16 +931,33 @@ def bench_update(args, G, torch, dev, world, rank):
         upd_ms.append(d.stats()["update_ms"])
         d.sensor_weights(parts, bo, obs, m, w["D"], logw=logw)
     timed = Timer(world, dev)
-    ms = timed(step, args.steps, args.warmup)
+    with ClockSampler(dev.index) as clk:
+        ms = timed(step, steps, warmup)
+    clocks = clk.summary(timed.window)
     ms_step = max_over_ranks(world, statistics.mean(ms))
-    qms = timed(lambda: d.sensor_weights(parts, bo, obs, m, w["D"], logw=logw), args.steps, 2)
+    qms = timed(lambda: d.sensor_weights(parts, bo, obs, m, w["D"], logw=logw), steps, 2)
     rays = parts.shape[0] * bo.numel()
-    line = base_line(args, world, world * rays / (ms_step * 1e-3), ms_step, "update4000",
-                     {"writes_per_step": int(w["writes"][0][0].shape[0])})
-    line.update({"update_ms_mean": statistics.mean(upd_ms[args.warmup:] or upd_ms),
-                 "query_only_rays_per_s": rays / (statistics.mean(qms) * 1e-3), "build_ms": st["build_ms"],
-                 "prune_ms": prune_ms, "zero_points": st["n_zero_points"], "store_bytes": st["store_bytes"]})
-    return line
+    st2 = d.stats()
+    d.close()
+    return {"rays_per_s": world * rays / (ms_step * 1e-3), "ms_per_step": ms_step, "rays_per_step": rays,
+            "writes_per_step": int(w["writes"][0][0].shape[0]),
+            "update_ms_per_1e4_writes": statistics.mean(upd_ms[warmup:] or upd_ms),
+            "query_only_rays_per_s": rays / (statistics.mean(qms) * 1e-3), "build_ms": st["build_ms"],
+            "prune_ms": prune_ms, "zero_points": st2["n_zero_points"], "store_bytes": st2["store_bytes"],
+            "clocks": clocks}
+
+
+MEASURES = {"rects256": measure_rects, "batched64": measure_batched64, "diff2000": measure_diff,
+            "update4000": measure_update}
+
+
+def bench_other(name):
+    def run(args, G, torch, dev, world, rank):
+        r = MEASURES[name](G, torch, dev, world, rank, args.steps, args.warmup)
+        line = base_line(args, world, r.pop("rays_per_s"), r.pop("ms_per_step"), name, {"launch": r.pop("launch")})
+        line.update({"gpu_launches": args.steps, **r})
+        return line
+    return run
 
 
 def run_gpu(args):
@@ -819,8 +967,7 @@ def run_gpu(args):
     G.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    fn = {"corridor2000": bench_corridor, "rects256": bench_rects, "batched64": bench_batched64,
-          "diff2000": bench_diff, "update4000": bench_update}[args.workload]
+    fn = bench_corridor if args.workload == "corridor2000" else bench_other(args.workload)
     line = fn(args, G, torch, dev, world, rank)
     if rank == 0:
         print(json.dumps(line))
@@ -848,11 +995,39 @@ def run_profile_update(args):
     return 0
 
 
+def run_profile_refine(args):
+    """A short run for ncu: warmup + steps one-launch refinements of the
+    diff2000 workload (10 steps each)."""
+    import torch
+    from paper_1705_01167_gb300 import cddt as G
+    w = WL.diff2000()
+    dev = torch.device("cuda", 0)
+    d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], w["max_range"])
+    m = G.beam_model(w["max_range"])
+    filters = []
+    for sc in w["scans"]:
+        r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], sc["beam_off"])).to(dev)).cpu().numpy()
+        obs = torch.from_numpy(np.clip(r + sc["noise"], 0, w["max_range"]).astype(np.float32)).to(dev)
+        P = sc["parts"].shape[0]
+        filters.append(dict(map=d, particles=torch.from_numpy(sc["parts"]).to(dev),
+                            beam_off=torch.from_numpy(sc["beam_off"]).to(dev), obs=obs, model=m,
+                            logw=torch.empty(P, device=dev), pair_offset=sc["D"],
+                            grad_xy=torch.empty((P, 2), device=dev), particles_out=torch.empty((P, 3), device=dev)))
+    plan = G.Plan(filters)
+    for _ in range(args.warmup + args.steps):
+        plan.refine(w["refine_steps"], w["eta"])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "refine", "logw0": float(filters[0]["logw"][0])}))
+    return 0
+
+
 def run_profile(args):
     """A short run for ncu: the batched launch (fixed shape), one per-filter
     pass and one sweep launch, a few launches each."""
     if args.profile_case == "update":
         return run_profile_update(args)
+    if args.profile_case == "refine":
+        return run_profile_refine(args)
     import torch
     from paper_1705_01167_gb300 import cddt as G
     w = WL.corridor2000()
@@ -863,7 +1038,11 @@ def run_profile(args):
     S, P = w["parts"].shape[:2]
     r = d.calc_range_many(torch.from_numpy(WL.gt_queries(w["gt"], bo)).to(dev)).cpu().numpy()
     obs = np.clip(r.reshape(S, bo.size) + w["noise"], 0, w["max_range"]).astype(np.float32)
-    parts_d = torch.from_numpy(w["parts"].reshape(-1, 3)).to(dev).contiguous()
+    parts = w["parts"]
+    if args.profile_case == "uniform":  # global localization: particles over the whole free space
+        parts = np.stack([synth.uniform_particles(w["grid"], P, seed=synth.SEED_PARTICLES + 5000 + t)
+                          for t in range(S)])
+    parts_d = torch.from_numpy(parts.reshape(-1, 3)).to(dev).contiguous()
     bo_d = torch.from_numpy(bo).to(dev)
     obs_d = torch.from_numpy(obs).to(dev).contiguous()
     logw_d = torch.empty(S * P, dtype=torch.float32, device=dev)
@@ -891,10 +1070,13 @@ def main():
     ap.add_argument("--impl", default="cddt", choices=["cddt", "reference"])
     ap.add_argument("--workload", default="corridor2000", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only: skip the other configurations' compact measurements")
+    ap.add_argument("--config-steps", type=int, default=10, help="timed steps of each other configuration")
     ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
-    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "u16", "update"],
-                    help="--profile workload: the corridor plan (u16: on the 16-bit store), or 10^4-write "
-                         "updates on the 4000^2 map")
+    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "u16", "uniform", "update", "refine"],
+                    help="--profile workload: the corridor plan (u16: on the 16-bit store; uniform: uniform "
+                         "particles), 10^4-write updates on the 4000^2 map, or the diff2000 refinement launch")
     ap.add_argument("--shape-tpp", type=int, default=1)
     ap.add_argument("--shape-ppi", type=int, default=512)
     ap.add_argument("--shape-block", type=int, default=512)

@@ -234,6 +234,9 @@ typedef struct {
     int32_t pair_offset;
     cddt_beam_model model;
     float *logw_dev; /* [P] */
+    /* outputs of cddt_plan_refine only (may be NULL otherwise): */
+    float *grad_xy_dev;       /* [P][2] d log w / d(x, y) at the refined pose */
+    float *particles_out_dev; /* [P][3] refined poses (may equal particles_dev) */
 } cddt_filter;
 
 typedef struct cddt_plan_s *cddt_plan;
@@ -264,6 +267,24 @@ CDDT_API cddt_status cddt_plan_get_shape(cddt_plan p, int32_t *tpp, int32_t *ppi
 /* Run the plan on `stream`: reset the queue and launch once.  Safe to
  * capture in a CUDA graph.  Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_plan_run(cddt_plan p, void *stream);
+
+/* Gradient pose refinement of every filter of the plan in one persistent
+ * launch per key type (the differentiation extension; the range is linear
+ * in the rotated abscissa, Section IV-B, so d log w / d(x, y) is the
+ * adjoint of cddt_sensor_weights_backward).  Each particle, with its pose
+ * held on chip, `steps` times evaluates log w and g = d log w / d(x, y) at
+ * its pose and moves (x, y) += eta g / max(|g|, 1e-12), each operation a
+ * correctly rounded float32 step in that order (theta is not changed); it
+ * then evaluates once more.  Written per filter: logw_dev (the final log w),
+ * grad_xy_dev (the final g) and particles_out_dev (the refined pose), which
+ * must be set for every filter with P > 0; particles_out_dev may equal
+ * particles_dev.  steps >= 0 (0: one forward + adjoint evaluation), eta >= 0,
+ * tpp: lanes per particle, 0 to choose from the plan's size, else 1, 2, 4,
+ * 8, 16 or 32 (results agree to float32 rounding of the per-particle sums
+ * across tpp).  Safe to capture in a CUDA graph once it has run outside one
+ * with the same tpp (its work table is uploaded on first use).
+ * Errors: ARG, CUDA. */
+CDDT_API cddt_status cddt_plan_refine(cddt_plan p, int32_t steps, float eta, int32_t tpp, void *stream);
 
 /* Capture cddt_plan_run into a CUDA graph owned by the plan and launch that
  * graph on later calls of cddt_plan_launch_graph.  The capture happens on

@@ -28,7 +28,7 @@ EXPORTED = (
     "cddt_build", "cddt_destroy", "cddt_prune", "cddt_update_cells", "cddt_calc_range_many",
     "cddt_sensor_weights", "cddt_sensor_weights_backward", "cddt_sensor_weights_fwd_bwd",
     "cddt_plan_create", "cddt_plan_autotune", "cddt_plan_set_shape", "cddt_plan_get_shape",
-    "cddt_plan_run", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
+    "cddt_plan_run", "cddt_plan_refine", "cddt_plan_launch_graph", "cddt_plan_items", "cddt_plan_destroy",
     "cddt_set_search", "cddt_get_stats", "cddt_get_status", "cddt_export", "cddt_export_grid",
     "cddt_sensor_work", "cddt_status_string", "cddt_version", "cddt_calc_range_many_noalloc", "cddt_plan_groups",
     "cddt_import", "cddt_gather_probe", "cddt_calc_range_timed", "cddt_motion", "cddt_resample",
@@ -78,7 +78,8 @@ class Filter(C.Structure):
     """cddt_filter: one filter of a plan (map handle, particles, scan, model, log-weights)."""
     _fields_ = [("map", C.c_void_p), ("particles_dev", C.c_void_p), ("P", C.c_int64),
                 ("beam_off_dev", C.c_void_p), ("obs_dev", C.c_void_p), ("B", C.c_int32),
-                ("pair_offset", C.c_int32), ("model", BeamModel), ("logw_dev", C.c_void_p)]
+                ("pair_offset", C.c_int32), ("model", BeamModel), ("logw_dev", C.c_void_p),
+                ("grad_xy_dev", C.c_void_p), ("particles_out_dev", C.c_void_p)]
 
 
 def library_path() -> str:
@@ -117,6 +118,7 @@ def load(build_if_missing: bool = True):
             "cddt_plan_set_shape": (st, [vp, i32, i32, i32, i32]),
             "cddt_plan_get_shape": (st, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
             "cddt_plan_run": (st, [vp, vp]),
+            "cddt_plan_refine": (st, [vp, i32, f32, i32, vp]),
             "cddt_plan_launch_graph": (st, [vp, vp]),
             "cddt_plan_items": (i64, [vp]),
             "cddt_plan_groups": (st, [vp, vp]),
@@ -699,9 +701,15 @@ class Plan:
             m: CDDT = f["map"]
             P, B = m._sensor_args(f["particles"], f["beam_off"], f["obs"], pinned_ok=True)
             _dev_or_pinned(f["logw"], torch.float32, "logw")
+            grad, pout = f.get("grad_xy"), f.get("particles_out")
+            if grad is not None:
+                _dev(grad, torch.float32, "grad_xy", (P, 2))
+            if pout is not None:
+                _dev(pout, torch.float32, "particles_out", (P, 3))
             arr[i] = Filter(m.handle.value, f["particles"].data_ptr(), P, f["beam_off"].data_ptr(),
                             f["obs"].data_ptr(), B, int(f.get("pair_offset", 0)), f["model"],
-                            f["logw"].data_ptr())
+                            f["logw"].data_ptr(), grad.data_ptr() if grad is not None else None,
+                            pout.data_ptr() if pout is not None else None)
             self._keep.append(f)
         h = C.c_void_p()
         _check(L.cddt_plan_create(arr, len(filters), _stream(stream), C.byref(h)), "cddt_plan_create")
@@ -726,6 +734,14 @@ class Plan:
     def run(self, stream=None):
         """cddt_plan_run: weight every filter of the plan in one persistent launch per key type."""
         _check(load().cddt_plan_run(self._h, _stream(stream)), "cddt_plan_run")
+
+    def refine(self, steps: int, eta: float, tpp: int = 0, stream=None):
+        """cddt_plan_refine: ``steps`` gradient pose refinement steps
+        (x, y) += eta g / |g| of every particle, then a final evaluation, in
+        one launch; writes each filter's ``logw``, ``grad_xy`` and
+        ``particles_out``."""
+        _check(load().cddt_plan_refine(self._h, int(steps), float(eta), int(tpp), _stream(stream)),
+               "cddt_plan_refine")
 
     def launch_graph(self, stream=None):
         """cddt_plan_launch_graph: the same as a CUDA graph (captured on first use)."""

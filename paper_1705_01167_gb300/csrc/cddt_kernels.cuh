@@ -46,6 +46,7 @@ struct SensorArgs {
     const float *grad_logw;
     float *grad_xy;
     unsigned long long *work;  // work-count mode: 6 counters
+    float *part_out;           // refined poses (plan refinement)
 };
 cddt_status launch_sensor(const cddt_s *h, const SensorArgs &a, int mode, cudaStream_t st);
 cddt_status calc_range(cddt_s *h, const float *pose, float *out, int64_t n, int sorted, cudaStream_t st);

@@ -510,7 +510,13 @@ struct cddt_plan_s {
     };
     std::vector<Launch> launches;
     std::vector<cddt::HotTable> tabs;  // one per launch
+    std::vector<std::vector<int32_t>> launch_filters;  // per launch, its filters in hot-table order
     int32_t n_queue = 0;              // queue counters allocated
+    // gradient refinement (cddt_plan_refine): its own items, blockDim / tpp
+    // particles each, per forward launch
+    cddt::WorkItem *refine_items_dev = nullptr;
+    int32_t refine_tpp = 0;
+    std::vector<Launch> refine_launches;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -538,6 +544,8 @@ static cddt_status plan_items(cddt_plan_s *p, cudaStream_t st)
     std::vector<WorkItem> items;
     p->launches.clear();
     p->tabs.clear();
+    p->launch_filters.clear();
+    p->refine_tpp = 0;  // the refinement items follow the launches
     for (int q = 0; q < 5; ++q) p->group_start[q] = 0;
     for (int q = 0; q < 4; ++q) {
         std::vector<int32_t> fl;
@@ -567,6 +575,7 @@ static cddt_status plan_items(cddt_plan_s *p, cudaStream_t st)
                              [](const WorkItem &a, const WorkItem &b) { return a.count > b.count; });
             p->launches.push_back({q, (int64_t)first, (int64_t)(items.size() - first)});
             p->tabs.push_back(tab);
+            p->launch_filters.emplace_back(fl.begin() + b0, fl.begin() + b0 + nb);
             p->group_start[q + 1] += (int64_t)(items.size() - first);
         }
     }
@@ -612,6 +621,8 @@ static cddt_status plan_upload(cddt_plan_s *p, cudaStream_t st)
         a.D = F.pair_offset;
         a.bc = make_beam_consts(F.model);
         a.logw = F.logw_dev;
+        a.grad_xy = F.grad_xy_dev;
+        a.part_out = F.particles_out_dev;
         d.a = a;
         fd[f] = d;
         p->gens[f] = F.map->generation;
@@ -681,6 +692,80 @@ cddt_status plan_run(cddt_plan_s *p, cudaStream_t st)
         if (blocks > count) blocks = count;
         fn<<<(unsigned)blocks, p->block, sm, st>>>(p->tabs[li], p->filters_dev, p->items_dev + first, count,
                                                    p->queue + li, p->max_B);
+    }
+    CDDT_CUDA(cudaGetLastError());
+    return CDDT_OK;
+}
+
+// Refinement items: the filters of every forward launch, cut into items of
+// kRefineBlock / tpp particles (one block's particles at once).
+constexpr int kRefineBlock = 256;
+static cddt_status refine_items(cddt_plan_s *p, int tpp, cudaStream_t st)
+{
+    std::vector<WorkItem> items;
+    p->refine_launches.clear();
+    const int per = kRefineBlock / tpp;
+    for (size_t li = 0; li < p->launches.size(); ++li) {
+        const size_t first = items.size();
+        const std::vector<int32_t> &fl = p->launch_filters[li];
+        for (size_t hot = 0; hot < fl.size(); ++hot) {
+            const int64_t P = p->filters[fl[hot]].P;
+            for (int64_t s0 = 0; s0 < P; s0 += per) {
+                WorkItem w{};
+                w.filter = fl[hot];
+                w.first = s0;
+                w.count = (int32_t)std::min<int64_t>(per, P - s0);
+                w.hot = (int32_t)hot;
+                items.push_back(w);
+            }
+        }
+        p->refine_launches.push_back({p->launches[li].q, (int64_t)first, (int64_t)(items.size() - first)});
+    }
+    if (p->refine_items_dev) cudaFree(p->refine_items_dev);
+    p->refine_items_dev = nullptr;
+    CDDT_CUDA(cudaMalloc(&p->refine_items_dev, sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
+    CDDT_CUDA(cudaMemcpyAsync(p->refine_items_dev, items.data(), sizeof(WorkItem) * items.size(),
+                              cudaMemcpyHostToDevice, st));
+    CDDT_CUDA(cudaStreamSynchronize(st));
+    p->refine_tpp = tpp;
+    return CDDT_OK;
+}
+
+cddt_status plan_refine(cddt_plan_s *p, int32_t steps, float eta, int32_t tpp, cudaStream_t st)
+{
+    bool rebuilt = false;
+    if (plan_stale(p)) {
+        cddt_status rc = plan_upload(p, st);
+        if (rc == CDDT_OK) rc = plan_items(p, st);
+        if (rc != CDDT_OK) return rc;
+        rebuilt = true;
+    }
+    if (tpp == 0) {  // lanes per particle: enough threads to fill the GPU
+        int64_t total = 0;
+        for (const cddt_filter &F : p->filters) total += std::max<int64_t>(F.P, 0);
+        const int64_t want = ((int64_t)sm_count() * 2048 + std::max<int64_t>(total, 1) - 1) / std::max<int64_t>(total, 1);
+        tpp = 1;
+        while (tpp < want && tpp < 32) tpp <<= 1;
+    }
+    if (rebuilt || p->refine_tpp != tpp || !p->refine_items_dev) {
+        cddt_status rc = refine_items(p, tpp, st);
+        if (rc != CDDT_OK) return rc;
+    }
+    CDDT_CUDA(cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long) * p->n_queue, st));
+    RefineFn fn0 = refine_fn(false, tpp), fn1 = refine_fn(true, tpp);
+    if (!fn0 || !fn1) return CDDT_ERR_ARG;
+    const size_t sm = beam_smem(p->max_B);
+    for (size_t li = 0; li < p->refine_launches.size(); ++li) {
+        const int64_t first = p->refine_launches[li].first, count = p->refine_launches[li].count;
+        if (count == 0) continue;
+        RefineFn fn = p->refine_launches[li].q >= 2 ? fn1 : fn0;
+        if (sm > 48 * 1024) CDDT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int blocks_per_sm = 0;
+        CDDT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, kRefineBlock, sm));
+        int64_t blocks = (int64_t)std::max(blocks_per_sm, 1) * sm_count();
+        if (blocks > count) blocks = count;
+        fn<<<(unsigned)blocks, kRefineBlock, sm, st>>>(p->tabs[li], p->filters_dev, p->refine_items_dev + first,
+                                                        count, p->queue + li, steps, eta);
     }
     CDDT_CUDA(cudaGetLastError());
     return CDDT_OK;
@@ -823,6 +908,18 @@ cddt_status cddt_plan_launch_graph(cddt_plan p, void *stream)
     return cddt::plan_launch_graph(p, (cudaStream_t)stream);
 }
 
+cddt_status cddt_plan_refine(cddt_plan p, int32_t steps, float eta, int32_t tpp, void *stream)
+{
+    CDDT_RANGE("cddt_plan_refine", stream);
+    if (!p) return CDDT_ERR_ARG;
+    if (steps < 0 || !(eta >= 0.0f) || !(eta < 1e30f)) return CDDT_ERR_ARG;
+    if (!(tpp == 0 || tpp == 1 || tpp == 2 || tpp == 4 || tpp == 8 || tpp == 16 || tpp == 32)) return CDDT_ERR_ARG;
+    for (const cddt_filter &F : p->filters)
+        if (F.P > 0 && (!F.grad_xy_dev || !F.particles_out_dev)) return CDDT_ERR_ARG;
+    CDDT_FAULT_POINT("cddt_plan_refine");
+    return cddt::plan_refine(p, steps, eta, tpp, (cudaStream_t)stream);
+}
+
 int64_t cddt_plan_items(cddt_plan p) { return p ? p->n_items : -1; }
 
 cddt_status cddt_plan_groups(cddt_plan p, int64_t *items_per_group)
@@ -840,6 +937,7 @@ cddt_status cddt_plan_destroy(cddt_plan p)
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->filters_dev) cudaFree(p->filters_dev);
     if (p->items_dev) cudaFree(p->items_dev);
+    if (p->refine_items_dev) cudaFree(p->refine_items_dev);
     if (p->queue) cudaFree(p->queue);
     delete p;
     return CDDT_OK;

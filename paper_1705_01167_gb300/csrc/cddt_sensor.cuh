@@ -40,21 +40,15 @@ __device__ __forceinline__ int sorted_sectors(int kb, int kps)
 // One particle's beams in traversal slots t = lane, lane + TPP, ... ; smem
 // holds one float4 {phi, z, s_lz, c_mr} per beam.  acc sums log2 p.
 // m and bc are read where they lie (kernel parameters or shared memory); the
-// particle poses come from `part`, ranges (forward mode, optional) go to
-// `ranges`.
+// particle's pose (x, y, th) is held in registers, ranges (forward mode,
+// optional) go to `ranges`.
 template <typename KT, int MODE, int SEARCH>
-__device__ __forceinline__ void particle_slots(const MapView &m, const BeamConsts &bc, int B, int D,
-                                               const float *part, float *ranges, const float *sh, int64_t p,
-                                               bool valid, int lane, int TPP, uint64_t pol, float &acc, float &gx,
-                                               float &gy, WorkAcc &w, bool &ok_out)
+__device__ __forceinline__ void particle_slots_at(const MapView &m, const BeamConsts &bc, int B, int D, float x,
+                                                  float y, float th, float *ranges, const float *sh, int64_t p,
+                                                  bool valid, int lane, int TPP, uint64_t pol, float &acc,
+                                                  float &gx, float &gy, WorkAcc &w, bool &ok_out)
 {
     const int T = D > 0 ? D : B;
-    float x = 0.f, y = 0.f, th = 0.f;
-    if (valid) {
-        x = __ldg(part + 3 * p);
-        y = __ldg(part + 3 * p + 1);
-        th = __ldg(part + 3 * p + 2);
-    }
     const bool ok = valid && free_cell(m.grid, m.W, m.H, x, y);
     ok_out = ok;
     const float4 *bt = reinterpret_cast<const float4 *>(sh);
@@ -139,6 +133,23 @@ __device__ __forceinline__ void particle_slots(const MapView &m, const BeamConst
             if (MODE == MODE_FWD && ranges && valid) ranges[p * B + j] = cj.r;
         }
     }
+}
+
+// The same with the pose read from part[3 p .. 3 p + 2].
+template <typename KT, int MODE, int SEARCH>
+__device__ __forceinline__ void particle_slots(const MapView &m, const BeamConsts &bc, int B, int D,
+                                               const float *part, float *ranges, const float *sh, int64_t p,
+                                               bool valid, int lane, int TPP, uint64_t pol, float &acc, float &gx,
+                                               float &gy, WorkAcc &w, bool &ok_out)
+{
+    float x = 0.f, y = 0.f, th = 0.f;
+    if (valid) {
+        x = __ldg(part + 3 * p);
+        y = __ldg(part + 3 * p + 1);
+        th = __ldg(part + 3 * p + 2);
+    }
+    particle_slots_at<KT, MODE, SEARCH>(m, bc, B, D, x, y, th, ranges, sh, p, valid, lane, TPP, pol, acc, gx, gy,
+                                        w, ok_out);
 }
 
 __device__ __forceinline__ void stage_beams(const BeamConsts &bc, int B, const float *obs, const float *beam_off,
@@ -296,6 +307,103 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
 }
 
 inline size_t beam_smem(int B) { return sizeof(float) * 4 * (size_t)B; }
+
+// One step of gradient pose refinement: (x, y) += eta g / max(|g|, 1e-12),
+// every operation correctly rounded in this order (no contraction).
+__device__ __forceinline__ void refine_move(float &x, float &y, float gx, float gy, float eta)
+{
+    const float n = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
+    const float s = __fdiv_rn(eta, fmaxf(n, 1e-12f));
+    x = __fadd_rn(x, __fmul_rn(gx, s));
+    y = __fadd_rn(y, __fmul_rn(gy, s));
+}
+
+// Gradient pose refinement of a plan's filters in one persistent launch (the
+// differentiation extension): every particle keeps its pose in registers
+// and, `steps` times, evaluates log w and g = d log w / d(x, y) at the pose
+// (the forward and adjoint traversal of the sensor model, one pass) and
+// moves by refine_move; then it evaluates once more.  Written per particle:
+// the final log w, the final g and the refined pose (theta unchanged).  TPP
+// lanes share a particle's traversal slots and their sums (butterfly
+// shuffles, so every lane holds the same g and takes the same step).  Items
+// (filter, particle range of blockDim.x / TPP) come from an atomic queue;
+// no block waits on another.
+template <typename KT, int TPP>
+__global__ void __launch_bounds__(256, 4)
+    refine_kernel(const __grid_constant__ HotTable tab, const FilterDev *filters, const WorkItem *items,
+                  int64_t n_items, unsigned long long *queue, int32_t steps, float eta)
+{
+    extern __shared__ __align__(16) float sh[];
+    __shared__ long long cur;
+    __shared__ __align__(16) FilterDev F;
+    const uint64_t pol = policy_evict_last();
+    const int lane = threadIdx.x % TPP;
+    const int group = threadIdx.x / TPP;
+    constexpr int kWords = (int)(sizeof(FilterDev) / sizeof(int4));
+    for (;;) {
+        if (threadIdx.x == 0) cur = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const long long it = cur;
+        if (it >= n_items) break;
+        const WorkItem wi = items[it];
+        for (int q = threadIdx.x; q < kWords; q += blockDim.x)
+            reinterpret_cast<int4 *>(&F)[q] = reinterpret_cast<const int4 *>(filters + wi.filter)[q];
+        __syncthreads();
+        const HotFilter &H = tab.f[wi.hot];
+        stage_beams(H.bc, H.B, F.a.obs, F.a.beam_off, sh);
+        __syncthreads();
+        const int64_t p = wi.first + group;
+        const bool valid = group < wi.count;
+        float x = 0.f, y = 0.f, th = 0.f;
+        if (valid) {
+            x = __ldg(F.a.part + 3 * p);
+            y = __ldg(F.a.part + 3 * p + 1);
+            th = __ldg(F.a.part + 3 * p + 2);
+        }
+        WorkAcc w;
+        float acc = 0.f, gx = 0.f, gy = 0.f;
+        for (int s = 0; s <= steps; ++s) {
+            acc = gx = gy = 0.f;
+            bool ok;
+            particle_slots_at<KT, MODE_FWDBWD, CDDT_SEARCH_TREE>(H.m, H.bc, H.B, H.D, x, y, th, nullptr, sh, p,
+                                                                 valid, lane, TPP, pol, acc, gx, gy, w, ok);
+            acc = group_sum<TPP>(acc);
+            gx = group_sum<TPP>(gx);
+            gy = group_sum<TPP>(gy);
+            if (s < steps) refine_move(x, y, gx, gy, eta);
+        }
+        if (lane == 0 && valid) {
+            F.a.logw[p] = acc * kLn2;
+            F.a.grad_xy[2 * p] = gx;
+            F.a.grad_xy[2 * p + 1] = gy;
+            F.a.part_out[3 * p] = x;
+            F.a.part_out[3 * p + 1] = y;
+            F.a.part_out[3 * p + 2] = th;
+        }
+        __syncthreads();
+    }
+}
+
+typedef void (*RefineFn)(const HotTable, const FilterDev *, const WorkItem *, int64_t, unsigned long long *,
+                         int32_t, float);
+
+template <typename KT>
+inline RefineFn refine_fn_kt(int tpp)
+{
+    switch (tpp) {
+    case 1: return refine_kernel<KT, 1>;
+    case 2: return refine_kernel<KT, 2>;
+    case 4: return refine_kernel<KT, 4>;
+    case 8: return refine_kernel<KT, 8>;
+    case 16: return refine_kernel<KT, 16>;
+    case 32: return refine_kernel<KT, 32>;
+    default: return nullptr;
+    }
+}
+
+// Kernel pointer of the refinement kernel for a key type and lanes per
+// particle (cddt_refine.cu); nullptr for an unknown tpp.
+RefineFn refine_fn(bool u16, int tpp);
 
 typedef void (*BatchedFn)(const HotTable, const FilterDev *, const WorkItem *, int64_t, unsigned long long *,
                           int32_t);

@@ -81,3 +81,17 @@ def test_json_line_fields():
     json.dumps(line)  # serialisable
     h = bench.host_cpu()
     assert h["nproc"] >= 1
+
+
+def test_recorded_counts_of_other_launches_follow_their_kernel_source(monkeypatch):
+    # the uniform-particle launch of batched_kernel is gated on that kernel's
+    # sources too, and carries its L1 wavefronts and DRAM bytes per particle
+    rec = bench.recorded("batched_kernel_uniform")
+    d = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    if d["batched_kernel_uniform"]["source_sha"] == bench.kernel_source_sha("batched_kernel"):
+        assert rec["l1_wavefronts_per_unit"] > 0 and rec["dram_bytes_per_unit"] > 0
+    else:
+        assert rec is None
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda k: "0" * 16)
+    assert bench.recorded("batched_kernel_uniform") is None
+    assert bench.recorded("batched_kernel") is None

@@ -187,6 +187,67 @@ def test_corridor2000_differentiation(G, oracle):
         assert logw_close(lw.cpu().numpy(), o.sensor_weights(xs, sc["beam_off"], obs, om, nthreads=16))
 
 
+def refine_move(x, g, eta):
+    """One refinement step as cddt_plan_refine takes it, in float32:
+    (x, y) += eta g / max(|g|, 1e-12), each operation correctly rounded."""
+    x = np.array(x, np.float32, copy=True)
+    gx, gy = g[:, 0].astype(np.float32), g[:, 1].astype(np.float32)
+    n = np.sqrt(gx * gx + gy * gy)
+    s = np.float32(eta) / np.maximum(n, np.float32(1e-12))
+    x[:, 0] = x[:, 0] + gx * s
+    x[:, 1] = x[:, 1] + gy * s
+    return x
+
+
+def test_corridor2000_plan_refinement(G, oracle):
+    """The diff2000 workload through one plan: both filters (4096 x 61 and
+    1024 x 1081 beams) take their 10 gradient refinement steps in one launch
+    (cddt_plan_refine).  Every step is checked: the run of k steps ends at the
+    pose of the run of k - 1 steps moved by that run's own gradient (bit for
+    bit), and its log-weights and gradients match the float64 oracle at that
+    pose; lanes per particle 1, 8 and the automatic choice agree."""
+    w = WL.diff2000()
+    o = oracle.OracleCDDT(w["grid"], w["theta_disc"], w["max_range"])
+    d = G.CDDT(dev(w["grid"]), w["theta_disc"], w["max_range"])
+    m, om = G.beam_model(w["max_range"]), oracle.beam_model(w["max_range"])
+    filters, host = [], []
+    for sc in w["scans"]:
+        r = o.calc_range(WL.gt_queries(w["gt"], sc["beam_off"]), nthreads=16)
+        obs = obs_from(r, sc["noise"], w["max_range"])
+        P = sc["parts"].shape[0]
+        filters.append(dict(map=d, particles=dev(sc["parts"]), beam_off=dev(sc["beam_off"]), obs=dev(obs), model=m,
+                            logw=torch.empty(P, device="cuda"), pair_offset=sc["D"],
+                            grad_xy=torch.empty((P, 2), device="cuda"),
+                            particles_out=torch.empty((P, 3), device="cuda")))
+        host.append((sc, obs))
+    plan = G.Plan(filters)
+    eta = w["eta"]
+    for tpp in (0, 1, 8):
+        prev = None
+        for k in range(w["refine_steps"] + 1 if tpp == 0 else 3):
+            plan.refine(k, eta, tpp=tpp)
+            torch.cuda.synchronize()
+            cur = []
+            for f, (sc, obs) in zip(filters, host):
+                x = f["particles_out"].cpu().numpy()
+                g = f["grad_xy"].cpu().numpy()
+                lw = f["logw"].cpu().numpy()
+                assert np.array_equal(x[:, 2].view(np.uint32), sc["parts"][:, 2].view(np.uint32))
+                want, scale = o.sensor_grad(x, sc["beam_off"], obs, om, nthreads=16)
+                assert grad_close(g, want, scale), (tpp, k, sc["B"])
+                assert logw_close(lw, o.sensor_weights(x, sc["beam_off"], obs, om, nthreads=16)), (tpp, k, sc["B"])
+                cur.append((x, g))
+            if prev is not None:
+                for (x0, g0), (x1, _) in zip(prev, cur):
+                    assert bits_equal(x1, refine_move(x0, g0, eta)), (tpp, k)
+            prev = cur
+        if tpp == 0:  # the refined poses moved: ten steps of 0.1 cell
+            moved = np.linalg.norm(prev[0][0][:, :2] - host[0][0]["parts"][:, :2], axis=1)
+            assert np.median(moved) > 0.5
+    plan.close()
+    d.close()
+
+
 # ------------------------------------------------------------------ 4000 x 4000 updates
 
 def test_update4000(G, oracle):
