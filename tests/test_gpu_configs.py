@@ -38,8 +38,13 @@ def logw_close(got, want, rtol=1e-5):
 
 
 def grad_close(got, want, scale, rtol=1e-5):
+    """Within rtol of the float64 oracle relative to the sum of the per-beam
+    term magnitudes, and relative to |g| where that sum is at most 10 |g|."""
     err = np.linalg.norm(np.asarray(got, np.float64) - want, axis=1)
-    return np.all(err <= rtol * np.maximum(np.linalg.norm(scale, axis=1), 1e-6))
+    gn, sn = np.linalg.norm(want, axis=1), np.linalg.norm(scale, axis=1)
+    mild = (gn > 0) & (sn <= 10 * gn)
+    return (np.all(err <= rtol * np.maximum(sn, 1e-6)) and mild.sum() >= len(gn) // 2
+            and np.all(err[mild] <= rtol * gn[mild]))
 
 
 def obs_from(ranges, noise, mr):

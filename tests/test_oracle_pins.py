@@ -326,6 +326,76 @@ def test_radial_pairing(oracle):
 
 # ------------------------------------------------------------------ approximation
 
+def test_exact_caster_closed_forms(oracle):
+    """The exact voxel-traversal caster (O3, Amanatides & Woo) on rays whose
+    answers are known by hand.  Mode 0 returns the distance along the ray to
+    the projection of the first crossed occupied cell's centre, mode 1 the
+    distance to the ray's entry point into that cell.
+    (a) Axis rays in a box with 1-cell border walls from a fractional start:
+    +x hits column W-1 (mode 0: W-1-x, mode 1: W-1.5-x), -x column 0 (x and
+    x - 0.5), and likewise in y; a pillar in the way is hit first.
+    (b) The start cell is the nearest cell centre: from x = 3.49 the pillar at
+    column 4 is one cell away, from x = 3.51 the start is the pillar (range 0).
+    A wall entered within max_range whose centre projects beyond it returns
+    max_range in mode 0.
+    (c) Rays from a cell centre just either side of 45 degrees pass next to
+    cell corners: with only the cells just above the diagonal occupied, a ray
+    a hair above 45 degrees crosses the y face first, into (i, i + 1) at
+    t = 0.5 / sin(theta) (mode 1; mode 0: its centre projects to sin(theta)),
+    while one a hair below crosses x faces first all the way and meets
+    nothing (max_range).  Through a checkerboard of occupied (i + j odd)
+    cells a 45-degree ray from (i + 0.1, j - 0.2) leaves through the x face
+    first, into cell (i + 1, j) at t = 0.4 / cos 45 (mode 1), whose centre
+    projects to 1.1 cos 45 (mode 0).
+    (d) A sloped ray to a vertical wall at column 20 enters it through the
+    wall's left face at t = (19.5 - x) / cos(theta) (mode 1); mode 0 is the
+    projection of the centre of the wall cell in the row the ray is in
+    there."""
+    W, H = 30, 20
+    box = np.zeros((H, W), np.uint8)
+    box[0, :] = box[-1, :] = box[:, 0] = box[:, -1] = 1
+    x, y, mr = 7.3, 11.6, 100.0
+    rays = [(0.0, W - 1 - x, W - 1.5 - x), (math.pi, x, x - 0.5), (math.pi / 2, H - 1 - y, H - 1.5 - y),
+            (1.5 * math.pi, y, y - 0.5)]
+    for th, want0, want1 in rays:
+        q = np.array([[x, y, th]])
+        assert oracle.cast_exact(box, q, mr, 0)[0] == pytest.approx(want0, abs=1e-9), th
+        assert oracle.cast_exact(box, q, mr, 1)[0] == pytest.approx(want1, abs=1e-9), th
+    pillar = box.copy()
+    pillar[12, 4] = 1  # column 4, row 12 (the row of y = 11.6)
+    q = np.array([[1.2, 11.6, 0.0], [3.49, 11.6, 0.0], [3.51, 11.6, 0.0]])
+    assert np.allclose(oracle.cast_exact(pillar, q, mr, 0), [4 - 1.2, 4 - 3.49, 0.0], atol=1e-9)
+    assert np.allclose(oracle.cast_exact(pillar, q, mr, 1), [3.5 - 1.2, 3.5 - 3.49, 0.0], atol=1e-9)
+    # the short ray ends at max_range; a wall entered within max_range whose
+    # centre projects beyond it is clamped to max_range (mode 0)
+    assert oracle.cast_exact(box, np.array([[x, y, 0.0]]), 5.0, 1)[0] == 5.0
+    assert oracle.cast_exact(box, np.array([[x, y, 0.0]]), W - 1.4 - x, 0)[0] == pytest.approx(W - 1.4 - x)
+    assert oracle.cast_exact(box, np.array([[x, y, 0.0]]), W - 1.4 - x, 1)[0] == pytest.approx(W - 1.5 - x)
+    # (c) the diagonal's corners, then a checkerboard
+    ii, jj = np.meshgrid(np.arange(16), np.arange(16))
+    stair = (jj == ii + 1).astype(np.uint8)
+    up, down = math.pi / 4 + 1e-6, math.pi / 4 - 1e-6
+    q = np.array([[5.0, 5.0, up], [5.0, 5.0, down]])
+    assert np.allclose(oracle.cast_exact(stair, q, mr, 1), [0.5 / math.sin(up), mr], atol=1e-9)
+    assert np.allclose(oracle.cast_exact(stair, q, mr, 0), [math.sin(up), mr], atol=1e-9)
+    cb = ((ii + jj) % 2).astype(np.uint8)
+    c45 = math.cos(math.pi / 4)
+    i0, j0 = 6, 8  # i + j even: free
+    q = np.array([[i0 + 0.1, j0 - 0.2, math.pi / 4]])
+    assert oracle.cast_exact(cb, q, mr, 1)[0] == pytest.approx(0.4 / c45, abs=1e-9)
+    assert oracle.cast_exact(cb, q, mr, 0)[0] == pytest.approx(1.1 * c45, abs=1e-9)
+    # (d) sloped ray to a vertical wall
+    wall = np.zeros((40, 40), np.uint8)
+    wall[:, 20] = 1
+    for (x0, y0, th) in ((2.3, 4.6, math.atan2(1, 3)), (5.7, 30.2, -0.4), (11.0, 19.5, 0.05)):
+        t1 = (19.5 - x0) / math.cos(th)
+        row = math.floor(y0 + t1 * math.sin(th) + 0.5)
+        t0 = (20 - x0) * math.cos(th) + (row - y0) * math.sin(th)
+        q = np.array([[x0, y0, th]])
+        assert oracle.cast_exact(wall, q, mr, 1)[0] == pytest.approx(t1, abs=1e-9), (x0, y0, th)
+        assert oracle.cast_exact(wall, q, mr, 0)[0] == pytest.approx(t0, abs=1e-9), (x0, y0, th)
+
+
 def test_against_exact_caster(oracle):
     """The CDDT is an approximation (Section II, III).  At a discrete direction
     a cell counts as hit when its rotated square meets the query's bin, a
