@@ -383,8 +383,12 @@ CDDT_API cddt_status cddt_motion(float *particles_dev, int64_t P, const int64_t 
  * w_i = exp(logw_i - max logw) and running sums C_i in double; output
  * particle m of a filter of n particles is input particle
  * i = min{ i : C_i > (u0 + m) / n * C_{n-1} } (the last one if none).
- * particles_dev float [P][3] and logw_dev float [P] (at least one finite
- * log-weight per filter) in, out_dev float [P][3] (not particles_dev) out,
+ * Where exp(logw - max) is undefined: a filter with no log-weight above
+ * -inf (all -inf or NaN) weighs every particle 1 (each is kept once, in
+ * order); otherwise a NaN log-weight weighs 0, and when the largest is +inf
+ * exactly the +inf particles weigh 1.
+ * particles_dev float [P][3] and logw_dev float [P] in, out_dev float
+ * [P][3] (not particles_dev) out,
  * index_dev int32 [P] (optional, NULL to skip) the chosen input index
  * within the filter, u0_dev float [F] one uniform offset in [0, 1) per
  * filter, scratch_dev double [P] the running sums.  Errors: ARG, CUDA. */

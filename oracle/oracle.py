@@ -297,11 +297,29 @@ def motion(particles, seg_start, odom, noise) -> np.ndarray:
     return out.astype(np.float32)
 
 
+def resample_weights(lw):
+    """Weights of one filter's log-weights (float64): exp(lw - max lw).  Where
+    that is undefined (reading R1): if no log-weight is above -inf (all -inf
+    or NaN, no particle has weight) every particle weighs 1; otherwise NaN
+    weighs 0, and if the largest is +inf the +inf particles weigh 1 and the
+    rest 0."""
+    lw = np.asarray(lw, np.float64)
+    num = lw[~np.isnan(lw)]
+    top = num.max() if num.size else -np.inf
+    if top == -np.inf:
+        return np.ones(lw.shape[0])
+    if top == np.inf:
+        return (lw == np.inf).astype(np.float64)
+    w = np.exp(lw - top)
+    w[np.isnan(lw)] = 0.0
+    return w
+
+
 def resample_indices(logw, seg_start, u0):
     """Low-variance (systematic) resampling of every filter segment (Section
     I resamples by belief; the low-variance scheme is the reading used here):
-    w_i = exp(logw_i - max logw) and running sums C_i in float64, in index
-    order; output m of a filter of n particles takes the first input i with
+    w_i = exp(logw_i - max logw) (resample_weights: also where that is
+    undefined) and running sums C_i in float64, in index order; output m of a filter of n particles takes the first input i with
     C_i > (u0 + m) / n * C_{n-1} (the last one when none is).  Returns the
     within-filter indices [P] and, per output, the distance of its target
     from the nearest running sum relative to the total (a decision this
@@ -316,7 +334,7 @@ def resample_indices(logw, seg_start, u0):
         n = b - a
         if n <= 0:
             continue
-        w = np.exp(lw[a:b] - lw[a:b].max())
+        w = resample_weights(lw[a:b])
         C = np.cumsum(w)
         tot = C[-1]
         for m in range(n):

@@ -55,8 +55,20 @@ __global__ void motion_kernel(float *part, int64_t P, const int64_t *seg, int F,
 // w_i = exp(logw_i - max logw) and their running sums C_i in double, then
 // output m takes the first input i with C_i > (u0 + m) / P * C_{P-1}.  The
 // sums are taken per thread over a contiguous chunk and offset by a scan of
-// the chunk totals (a fixed order: the same bits on every run).
+// the chunk totals (a fixed order: the same bits on every run).  Weights
+// that exp(logw - max) leaves undefined: when no log-weight is above -inf
+// (all -inf or NaN: no particle has weight) every particle weighs 1;
+// otherwise a NaN log-weight weighs 0, and when the largest is +inf exactly
+// the +inf particles weigh 1.
 constexpr int kResampleThreads = 512;
+
+__device__ __forceinline__ double resample_weight(float lw, double m0)
+{
+    if (m0 == -__builtin_huge_val()) return 1.0;
+    if (isnan(lw)) return 0.0;
+    if (m0 == __builtin_huge_val()) return lw == __builtin_huge_valf() ? 1.0 : 0.0;
+    return exp((double)lw - m0);
+}
 
 __global__ void __launch_bounds__(kResampleThreads) resample_kernel(const float *part, const float *logw,
                                                                     const int64_t *seg, const float *u0,
@@ -86,7 +98,7 @@ __global__ void __launch_bounds__(kResampleThreads) resample_kernel(const float 
     const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
     const int64_t i0 = threadIdx.x * chunk, i1 = min(n, i0 + chunk);
     double s = 0.0;
-    for (int64_t i = i0; i < i1; ++i) s += exp((double)lw[i] - m0);
+    for (int64_t i = i0; i < i1; ++i) s += resample_weight(lw[i], m0);
     red[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -100,7 +112,7 @@ __global__ void __launch_bounds__(kResampleThreads) resample_kernel(const float 
     __syncthreads();
     double run = red[threadIdx.x];
     for (int64_t i = i0; i < i1; ++i) {
-        run += exp((double)lw[i] - m0);
+        run += resample_weight(lw[i], m0);
         C[i] = run;
     }
     __syncthreads();

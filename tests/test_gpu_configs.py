@@ -346,4 +346,21 @@ def test_batched64(G, oracle):
         idx = np.arange(0, parts.shape[0], 11)
         want = o.sensor_weights(parts[idx], w["beam_off"], obs, oracle.beam_model(mp["max_range"]), nthreads=16)
         assert logw_close(got[mi][idx], want), mi
+    # the largest map (side 4096 if drawn, the largest theta_disc among the
+    # largest sides): 96 sampled particles' ranges against the brute-force
+    # definition (every edge cell scanned, no store) bit for bit, and the
+    # batched launch's log-weights against the float64 beam model of them
+    big = max(range(len(w["maps"])), key=lambda i: (w["maps"][i]["grid"].size, w["maps"][i]["theta_disc"]))
+    mp = w["maps"][big]
+    parts, obs = per[big]
+    sel = np.unique(np.linspace(0, parts.shape[0] - 1, 96).astype(np.int64))
+    f = filters[big]
+    _, ranges = f["map"].sensor_weights(dev(parts[sel]), bo, f["obs"], f["model"], D, want_ranges=True)
+    q = np.concatenate([np.stack([np.full(61, parts[i, 0]), np.full(61, parts[i, 1]),
+                                  (parts[i, 2] + w["beam_off"]).astype(np.float32)], 1) for i in sel]).astype(np.float32)
+    p = oracle.Params(mp["grid"].shape[1], mp["grid"].shape[0], mp["theta_disc"], mp["max_range"])
+    brute = p.calc_range_brute(mp["grid"], q, nthreads=16)
+    assert bits_equal(ranges.cpu().numpy().reshape(-1), brute), (big, mp["grid"].shape, mp["theta_disc"])
+    pz, _ = oracle.beam_eval(oracle.beam_model(mp["max_range"]), np.tile(obs, sel.size), brute.astype(np.float64))
+    assert logw_close(got[big][sel], np.log(pz).reshape(sel.size, -1).sum(1)), big
     plan.close()

@@ -75,6 +75,28 @@ def test_resampling_matches_oracle(G, oracle):
     assert torch.equal(idx2, idx) and torch.equal(out2, out)
 
 
+def test_resampling_of_undefined_weights(G, oracle):
+    """Filters whose log-weights are all -inf, all NaN, partly NaN and partly
+    +inf: the same indices as the oracle (reading R1), and no NaN in the
+    output."""
+    sizes = [33, 40, 257, 64]
+    parts, seg, _, _ = _case(3, sizes)
+    rs = np.random.default_rng(9)
+    logw = rs.normal(-50.0, 3.0, parts.shape[0]).astype(np.float32)
+    logw[seg[0]:seg[1]] = -np.inf
+    logw[seg[1]:seg[2]] = np.nan
+    logw[seg[2]:seg[3]:4] = np.nan
+    logw[seg[3] + 7] = logw[seg[3] + 50] = np.inf
+    u0 = rs.uniform(0, 1, len(sizes)).astype(np.float32)
+    idx_t = torch.empty(parts.shape[0], dtype=torch.int32, device="cuda")
+    out, idx = G.resample(dev(parts), dev(logw), dev(seg), dev(u0), index=idx_t)
+    got = idx.cpu().numpy().astype(np.int64)
+    want, margin = oracle.resample_indices(logw, seg, u0)
+    assert np.array_equal(got[margin >= 1e-12], want[margin >= 1e-12])
+    assert np.array_equal(got[seg[0]:seg[2]], np.concatenate([np.arange(33), np.arange(40)]))
+    assert np.isfinite(out.cpu().numpy()).all()
+
+
 def test_filter_step_in_a_graph(G, oracle):
     """Motion, batched sensor weights and resampling of 3 filters as one
     CUDA graph, replayed: the same as the steps run one by one."""

@@ -728,6 +728,26 @@ def test_motion_model_pins():
     assert list(out[:, 0]) == [1.0, 1.0, 3.0, 3.0, 3.0]
 
 
+def test_resampling_of_undefined_weights():
+    """Reading R1 where exp(logw - max) is undefined: a filter whose every
+    log-weight is -inf (or NaN) has no weighted particle, so all weigh the
+    same and systematic resampling keeps each once, in order; a NaN among
+    finite log-weights is never drawn; +inf log-weights share every draw."""
+    from oracle import oracle as O
+    n = 40
+    for lw in (np.full(n, -np.inf, np.float32), np.full(n, np.nan, np.float32)):
+        idx, _ = O.resample_indices(lw, [0, n], np.array([0.6], np.float32))
+        assert np.array_equal(idx, np.arange(n))
+    lw = np.random.default_rng(7).normal(-30.0, 2.0, n).astype(np.float32)
+    lw[::3] = np.nan
+    idx, _ = O.resample_indices(lw, [0, n], np.array([0.2], np.float32))
+    assert not np.isnan(lw[idx]).any()
+    lw = np.full(n, -10.0, np.float32)
+    lw[[5, 21]] = np.inf
+    idx, _ = O.resample_indices(lw, [0, n], np.array([0.3], np.float32))
+    assert set(idx.tolist()) == {5, 21} and (idx == 5).sum() == n // 2
+
+
 def test_resampling_pins():
     """Systematic resampling: equal weights keep every particle once in
     order; one finite weight takes every draw; for any weights each particle
