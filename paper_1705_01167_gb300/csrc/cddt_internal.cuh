@@ -39,8 +39,9 @@ namespace cddt {
 
 constexpr float kInf = __builtin_huge_valf();
 
-// The first 16 bytes hold what a float32 query reads (one 16-byte load).
-struct __align__(16) SliceInfo {
+// The first 16 bytes hold what a float32 query reads (one 16-byte load); a
+// 16-bit query reads all 32 (one 32-byte load).
+struct __align__(32) SliceInfo {
     float c, s;      // cos, sin of theta_s
     uint32_t sbase;  // first global bin
     uint32_t Tnb;    // T | nb << 16 (both < 65536)
@@ -407,12 +408,9 @@ struct SearchResult {
 // directly; 16-bit keys compare as integers against the exact threshold:
 // value(key) = key / Q - X is exact in float32, so value(key) <= x iff
 // key <= floor((x + X) Q) and value(key) < x iff key <= ceil((x + X) Q) - 1.
-// The threshold is exact in float32 arithmetic: x + X = s + e exactly
-// (Knuth's TwoSum), Q is a power of two, and floor(sQ + eQ) is floor(sQ)
-// unless sQ is an integer, when it is sQ + floor(eQ) (|eQ| is at most half
-// an ulp of sQ, so it cannot cross an integer otherwise); likewise for
-// ceil.  (A float64 evaluation is as slow as the search on GB300, and not
-// exact when x and X differ by more than 29 binary orders.)
+// X is an integer and Q a power of two, so X Q is an integer and the
+// threshold is floor(x Q) + X Q (ceil(x Q) + X Q - 1), every step exact in
+// float32 (x + X itself would round).
 template <typename KT, bool Upper> struct Cmp;
 template <bool Upper> struct Cmp<float, Upper> {
     float x;
@@ -427,18 +425,11 @@ template <bool Upper> struct Cmp<uint16_t, Upper> {
     int t;
     __device__ __forceinline__ Cmp(const MapView &m, float x, float X)
     {
-        const float s = __fadd_rn(x, X);
-        const float bp = __fsub_rn(s, x);
-        const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bp)), __fsub_rn(X, bp));
-        const float f = __fmul_rn(s, m.Q), eq = __fmul_rn(e, m.Q);
-        float tt;
-        if (Upper) {
-            const float fl = floorf(f);
-            tt = fl == f ? __fadd_rn(f, floorf(eq)) : fl;
-        } else {
-            const float cl = ceilf(f);
-            tt = __fsub_rn(cl == f ? __fadd_rn(f, ceilf(eq)) : cl, 1.0f);
-        }
+        // floor((x + X) Q) = floor(x Q) + X Q because X Q is an integer; x Q
+        // is exact (Q a power of two >= 1) and, for a cast from inside the
+        // map, both sums are integers below 2^24 in magnitude, so exact too
+        const float f = __fmul_rn(x, m.Q), xq = __fmul_rn(X, m.Q);
+        const float tt = Upper ? __fadd_rn(floorf(f), xq) : __fsub_rn(__fadd_rn(ceilf(f), xq), 1.0f);
         t = (int)fminf(fmaxf(tt, -1.0f), 65536.0f);
     }
     __device__ __forceinline__ bool le(uint32_t key) const { return (int)key <= t; }
@@ -764,7 +755,18 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     const bool bwd = k >= S;
     const int s = bwd ? k - S : k;
     k_is_fwd = !bwd;
-    const float4 sa = __ldg(chk_slice(m, reinterpret_cast<const float4 *>(m.slices + s), 16));
+    // float32 keys read the slice record's first 16 bytes; 16-bit keys the
+    // whole 32 (the key offset X with it, one load)
+    float4 sa;
+    float X = 0.0f;
+    if constexpr (sizeof(KT) == 4) {
+        sa = __ldg(chk_slice(m, reinterpret_cast<const float4 *>(m.slices + s), 16));
+    } else {
+        uint32_t w[8];
+        ld_node(chk_slice(m, m.slices + s, 32), w);
+        sa = make_float4(__uint_as_float(w[0]), __uint_as_float(w[1]), __uint_as_float(w[2]), __uint_as_float(w[3]));
+        X = __uint_as_float(w[4]);
+    }
     const float c = sa.x, sn = sa.y;
     const uint32_t Tnb = __float_as_uint(sa.w);
     const int T = (int)(Tnb & 0xffffu), nb = (int)(Tnb >> 16);
@@ -777,7 +779,6 @@ __device__ __forceinline__ void cast_pair(const MapView &m, float x, float y, in
     f.kb = r.kb = -1;
     if (b >= 0 && b < nb) {
         const uint32_t g = __float_as_uint(sa.z) + (uint32_t)b;
-        const float X = sizeof(KT) == 4 ? 0.0f : __ldg(chk_slice(m, &m.slices[s].X, 4));
         int kb;
         if (!bwd || pair) {
             // forward: first key > x' (upper bound)

@@ -327,7 +327,17 @@ __global__ void __launch_bounds__(256) cast_records_kernel(MapView m, const uint
     float range = 0.0f;
     if (!(r.w & kRecZero)) {
         const int s = (int)(r.w & kRecSlice);
-        const float4 sa = __ldg(chk_slice(m, reinterpret_cast<const float4 *>(m.slices + s), 16));
+        float4 sa;
+        float X = 0.0f;
+        if constexpr (sizeof(KT) == 4) {
+            sa = __ldg(chk_slice(m, reinterpret_cast<const float4 *>(m.slices + s), 16));
+        } else {  // the whole 32-byte slice record, with the key offset X
+            uint32_t w[8];
+            ld_node(chk_slice(m, m.slices + s, 32), w);
+            sa = make_float4(__uint_as_float(w[0]), __uint_as_float(w[1]), __uint_as_float(w[2]),
+                             __uint_as_float(w[3]));
+            X = __uint_as_float(w[4]);
+        }
         float xr, yr;
         project(__uint_as_float(r.x), __uint_as_float(r.y), sa.x, sa.y, xr, yr);
         const uint32_t Tnb = __float_as_uint(sa.w);
@@ -335,7 +345,6 @@ __global__ void __launch_bounds__(256) cast_records_kernel(MapView m, const uint
         range = m.max_range;
         if (b >= 0 && b < (int)(Tnb >> 16)) {
             const uint32_t g = __float_as_uint(sa.z) + (uint32_t)b;
-            const float X = sizeof(KT) == 4 ? 0.0f : __ldg(chk_slice(m, &m.slices[s].X, 4));
             int kb;
             if (!(r.w & kRecReverse)) {  // forward: first key > x'
                 const SearchResult sr = bin_search<KT, true, SEARCH>(m, g, xr, X, pol, kb);
