@@ -98,7 +98,11 @@ __global__ void __launch_bounds__(kResampleThreads) resample_kernel(const float 
     const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
     const int64_t i0 = threadIdx.x * chunk, i1 = min(n, i0 + chunk);
     double s = 0.0;
-    for (int64_t i = i0; i < i1; ++i) s += resample_weight(lw[i], m0);
+    for (int64_t i = i0; i < i1; ++i) {  // the weights wait in C for the running sums
+        const double w = resample_weight(lw[i], m0);
+        C[i] = w;
+        s += w;
+    }
     red[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(kResampleThreads) resample_kernel(const float 
     __syncthreads();
     double run = red[threadIdx.x];
     for (int64_t i = i0; i < i1; ++i) {
-        run += resample_weight(lw[i], m0);
+        run += C[i];
         C[i] = run;
     }
     __syncthreads();
