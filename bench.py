@@ -917,12 +917,25 @@ def measure_diff(G, torch, dev, world, rank, steps, warmup):
 def measure_update(G, torch, dev, world, rank, steps, warmup):
     """update4000: 10^4 cell writes (5000 inserts, 5000 removes) through
     cddt_update_cells on a 4000 x 4000 map (theta_disc 360), then 100,000
-    particles x 61 beams; full build and prune (on a separate handle) times."""
+    particles x 61 beams; full build and prune (on a separate handle) times;
+    and a 10 M-query uniform sweep of the fresh map, unsorted and
+    slice-sorted."""
     w = WL.update4000(steps=steps + warmup, seed_offset=RK.seed_offset(rank))
     mr = w["max_range"]
     grid = torch.from_numpy(w["grid"]).to(dev)
     d = G.CDDT(grid, w["theta_disc"], mr)
     st = d.stats()
+    # a 10 M uniform sweep of the 2 GB store, unsorted and slice-sorted: with
+    # the store 16x the L2, each unsorted search misses at every level, and
+    # the sort's slice-by-slice order reads each slice's nodes about once
+    sw = torch.from_numpy(synth.uniform_queries(w["grid"], 10_000_000, seed=synth.SEED_PARTICLES + 4007)).to(dev)
+    sw_out = torch.empty(sw.shape[0], device=dev)
+    timed = Timer(world, dev)
+    ms_sw = timed(lambda: d.calc_range_many(sw, out=sw_out), 5, 2)
+    ms_so = timed(lambda: d.calc_range_many(sw, sort_by_slice=True, out=sw_out), 5, 2)
+    sweep = {"sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_sw) * 1e-3),
+             "sweep_sorted_rays_per_s": sw.shape[0] / (statistics.mean(ms_so) * 1e-3)}
+    del sw, sw_out
     dp = G.CDDT(grid, w["theta_disc"], mr)
     dp.prune()
     prune_ms = dp.stats()["prune_ms"]
@@ -941,7 +954,6 @@ def measure_update(G, torch, dev, world, rank, steps, warmup):
         d.update_cells(xy, occ)
         upd_ms.append(d.stats()["update_ms"])
         d.sensor_weights(parts, bo, obs, m, w["D"], logw=logw)
-    timed = Timer(world, dev)
     with ClockSampler(dev.index) as clk:
         ms = timed(step, steps, warmup)
     clocks = clk.summary(timed.window)
@@ -955,7 +967,8 @@ def measure_update(G, torch, dev, world, rank, steps, warmup):
             "update_ms_per_1e4_writes": statistics.mean(upd_ms[warmup:] or upd_ms),
             "query_only_rays_per_s": rays / (statistics.mean(qms) * 1e-3), "build_ms": st["build_ms"],
             "prune_ms": prune_ms, "zero_points": st2["n_zero_points"], "store_bytes": st2["store_bytes"],
-            "clocks": clocks}
+            **sweep, "clocks": clocks,
+            "launch": "cddt_update_cells (10^4 writes) then cddt_sensor_weights (100,000 x 61) per step"}
 
 
 MEASURES = {"rects256": measure_rects, "batched64": measure_batched64, "diff2000": measure_diff,
@@ -965,7 +978,8 @@ MEASURES = {"rects256": measure_rects, "batched64": measure_batched64, "diff2000
 def bench_other(name):
     def run(args, G, torch, dev, world, rank):
         r = MEASURES[name](G, torch, dev, world, rank, args.steps, args.warmup)
-        line = base_line(args, world, r.pop("rays_per_s"), r.pop("ms_per_step"), name, {"launch": r.pop("launch")})
+        line = base_line(args, world, r.pop("rays_per_s"), r.pop("ms_per_step"), name,
+                         {"launch": r.pop("launch", "")})
         line.update({"gpu_launches": args.steps, **r})
         return line
     return run
@@ -1032,11 +1046,32 @@ def run_profile_refine(args):
     return 0
 
 
+def run_profile_sweep4000(args):
+    """A short run for ncu: one unsorted and one slice-sorted 10 M uniform
+    sweep of the 4000 x 4000 map (theta_disc 360, 2 GB store), after
+    `warmup` of each."""
+    import torch
+    from paper_1705_01167_gb300 import cddt as G
+    g = synth.corridor_map(4000, 4000)
+    dev = torch.device("cuda", 0)
+    d = G.CDDT(torch.from_numpy(g).to(dev), 360, 1000.0)
+    sw = torch.from_numpy(synth.uniform_queries(g, 10_000_000, seed=synth.SEED_PARTICLES + 4007)).to(dev)
+    out = torch.empty(sw.shape[0], device=dev)
+    for _ in range(args.warmup + 1):
+        d.calc_range_many(sw, out=out)
+        d.calc_range_many(sw, sort_by_slice=True, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "sweep4000", "store_bytes": d.stats()["store_bytes"]}))
+    return 0
+
+
 def run_profile(args):
     """A short run for ncu: the batched launch (fixed shape), one per-filter
     pass and one sweep launch, a few launches each."""
     if args.profile_case == "update":
         return run_profile_update(args)
+    if args.profile_case == "sweep4000":
+        return run_profile_sweep4000(args)
     if args.profile_case == "refine":
         return run_profile_refine(args)
     import torch
@@ -1088,9 +1123,10 @@ def main():
                     help="default workload only: skip the other configurations' compact measurements")
     ap.add_argument("--config-steps", type=int, default=10, help="timed steps of each other configuration")
     ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
-    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "u16", "uniform", "update", "refine"],
+    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "u16", "uniform", "update", "refine", "sweep4000"],
                     help="--profile workload: the corridor plan (u16: on the 16-bit store; uniform: uniform "
-                         "particles), 10^4-write updates on the 4000^2 map, or the diff2000 refinement launch")
+                         "particles), 10^4-write updates on the 4000^2 map, the diff2000 refinement launch, "
+                         "or a 10 M sweep of the 4000^2 map, unsorted and slice-sorted")
     ap.add_argument("--shape-tpp", type=int, default=1)
     ap.add_argument("--shape-ppi", type=int, default=512)
     ap.add_argument("--shape-block", type=int, default=512)

@@ -95,3 +95,12 @@ def test_recorded_counts_of_other_launches_follow_their_kernel_source(monkeypatc
     monkeypatch.setattr(bench, "kernel_source_sha", lambda k: "0" * 16)
     assert bench.recorded("batched_kernel_uniform") is None
     assert bench.recorded("batched_kernel") is None
+
+
+def test_every_configuration_states_its_launch():
+    # each measure_* result names its launch (the standalone --workload line
+    # carries it in config.launch)
+    import inspect
+    for name, fn in bench.MEASURES.items():
+        src = inspect.getsource(fn)
+        assert '"launch":' in src, name
