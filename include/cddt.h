@@ -255,7 +255,7 @@ CDDT_API cddt_status cddt_plan_create(const cddt_filter *filters_host, int32_t n
  * Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_plan_autotune(cddt_plan p, void *stream);
 
-/* Set the launch shape by hand: tpp in {1,2,4,8} threads per particle, ppi
+/* Set the launch shape by hand: tpp in {1,2,4,8,16,32} threads per particle, ppi
  * particles per work item (multiple of 32 / tpp), block threads in {256,
  * 512}, regcap 0 (registers as the compiler needs) or 1 (capped so that 48
  * warps stay resident per SM).  Errors: ARG. */

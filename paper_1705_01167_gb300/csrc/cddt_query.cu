@@ -814,7 +814,7 @@ cddt_status plan_autotune(cddt_plan_s *p, cudaStream_t st)
     struct Shape { int tpp, ppi, block, regcap; };
     std::vector<Shape> cand;
     for (int regcap : {0, 1})
-        for (int tpp : {1, 2, 4, 8})
+        for (int tpp : {1, 2, 4, 8, 16, 32})
             for (int block : {256, 512})
                 for (int mult : {1, 2, 4}) {
                     int ppi = block / tpp * mult;
@@ -880,7 +880,7 @@ cddt_status cddt_plan_autotune(cddt_plan p, void *stream)
 cddt_status cddt_plan_set_shape(cddt_plan p, int32_t tpp, int32_t ppi, int32_t block, int32_t regcap)
 {
     if (!p) return CDDT_ERR_ARG;
-    if (!(tpp == 1 || tpp == 2 || tpp == 4 || tpp == 8)) return CDDT_ERR_ARG;
+    if (!(tpp == 1 || tpp == 2 || tpp == 4 || tpp == 8 || tpp == 16 || tpp == 32)) return CDDT_ERR_ARG;
     if (!(block == 256 || block == 512)) return CDDT_ERR_ARG;
     if (ppi < 1 || ppi % (32 / tpp)) return CDDT_ERR_ARG;
     if (regcap != 0 && regcap != 1) return CDDT_ERR_ARG;

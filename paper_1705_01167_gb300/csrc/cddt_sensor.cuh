@@ -468,4 +468,18 @@ inline BatchedFn batched_fn_kt(int tpp, int block)
     return nullptr;
 }
 
+// 16 and 32 lanes per particle, for plans with few particles (their own
+// translation units, cddt_batched_wide_*.cu, to keep compile times short).
+template <typename KT, int SEARCH, int WARPS>
+inline BatchedFn batched_fn_kt_wide(int tpp, int block)
+{
+#define CDDT_BF(T, B) if (tpp == T && block == B) return batched_kernel<KT, SEARCH, T, B, WARPS>;
+    CDDT_BF(16, 256) CDDT_BF(16, 512)
+    CDDT_BF(32, 256) CDDT_BF(32, 512)
+#undef CDDT_BF
+    return nullptr;
+}
+BatchedFn batched_fn_wide_f32(int search, int tpp, int block, int regcap);
+BatchedFn batched_fn_wide_u16(int search, int tpp, int block, int regcap);
+
 }  // namespace cddt

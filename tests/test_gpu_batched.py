@@ -69,12 +69,12 @@ def test_plan_run_matches_oracle(G, batch):
     maps, filters, refs = batch
     plan = G.Plan(filters)
     assert plan.items > len([f for f in filters if f["particles"].shape[0]])
-    for tpp in (1, 2, 4, 8):
+    for tpp in (1, 2, 4, 8, 16, 32):
         for block in (256, 512):
             for regcap in (0, 1):
                 for f in filters:
                     f["logw"].fill_(float("nan"))
-                plan.set_shape(tpp, block // tpp * 2 if tpp < 8 else 64, block, regcap)
+                plan.set_shape(tpp, block // tpp * 2 if tpp < 8 else 64 if tpp == 8 else block // tpp, block, regcap)
                 plan.run()
                 _check(filters, refs)
     plan.close()
@@ -84,7 +84,7 @@ def test_plan_autotune_and_graph(G, batch):
     maps, filters, refs = batch
     plan = G.Plan(filters)
     shape = plan.autotune()
-    assert shape["tpp"] in (1, 2, 4, 8)
+    assert shape["tpp"] in (1, 2, 4, 8, 16, 32)
     for f in filters:
         f["logw"].fill_(float("nan"))
     plan.launch_graph()
