@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -394,19 +395,33 @@ struct SortShape {
 
 // Blocks of the count and place passes that fit on one streaming
 // multiprocessor at once (both passes use the same blocks).
-static int sort_blocks_per_sm(int nbk)
+// Blocks of the count and place passes that fit on one streaming
+// multiprocessor at once, for the largest bucket count (the shared memory of
+// both passes grows with it), queried once per device; the first query also
+// raises both kernels' shared-memory limits.  0 when a query failed.
+static int sort_blocks_per_sm()
 {
+    constexpr int kDevices = 64;
+    static std::atomic<int> cached[kDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    if (dev < kDevices) {
+        const int v = cached[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
     int a = 0, b = 0;
     if (cudaFuncSetAttribute(sort_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)count_smem(kMaxSortBuckets)) != cudaSuccess ||
         cudaFuncSetAttribute(sort_place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)place_smem(kMaxSortBuckets)) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sort_count_kernel, kSortThreads, count_smem(nbk)) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sort_place_kernel, kSortThreads, place_smem(nbk)) !=
-            cudaSuccess)
-        return 1;
-    return std::max(1, std::min(a, b));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sort_count_kernel, kSortThreads,
+                                                      count_smem(kMaxSortBuckets)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sort_place_kernel, kSortThreads,
+                                                      place_smem(kMaxSortBuckets)) != cudaSuccess)
+        return 0;
+    const int v = std::max(1, std::min(a, b));
+    if (dev < kDevices) cached[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 static SortShape sort_shape(const cddt_s *h, int64_t n)
@@ -417,7 +432,7 @@ static SortShape sort_shape(const cddt_s *h, int64_t n)
     p.nbk = ((2 * h->S - 1) >> p.sh) + 1;
     // one wave of blocks, each a whole number of tiles
     const int64_t nn = std::max<int64_t>(n, 1);
-    const int64_t waves = (int64_t)sm_count() * sort_blocks_per_sm(p.nbk);
+    const int64_t waves = (int64_t)sm_count() * std::max(1, sort_blocks_per_sm());
     const int64_t tiles = (nn + kSortTile - 1) / kSortTile;
     p.chunk = ((tiles + waves - 1) / waves) * kSortTile;
     p.nblk = (nn + p.chunk - 1) / p.chunk;
@@ -449,7 +464,7 @@ cddt_status calc_range_sorted_into(cddt_s *h, const float *pose, float *out, int
     c += 4 * p.ncount;
     uint4 *rec = reinterpret_cast<uint4 *>(((uintptr_t)c + 15) & ~(uintptr_t)15);
     const MapView m = h->view();
-    // (sort_shape set both kernels' shared-memory limits)
+    if (sort_blocks_per_sm() == 0) return CDDT_ERR_CUDA;  // also raises the kernels' shared-memory limits
     sort_count_kernel<<<(unsigned)p.nblk, kSortThreads, count_smem(p.nbk), st>>>(m, pose, n, p.chunk, p.sh, p.nbk,
                                                                                  counts);
     exclusive_scan_u32(counts, counts, p.ncount, scan_part, total, st);
