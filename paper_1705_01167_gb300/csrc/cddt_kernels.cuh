@@ -154,14 +154,18 @@ __device__ __forceinline__ uint32_t key_bits(KT v)
     return (uint32_t)(*reinterpret_cast<const uint16_t *>(&v));
 }
 
-// Index one bin whose sorted keys sit in its leaf run (one warp, all lanes):
-// pad the last leaf, fill the internal levels with the largest key under
-// each child, and write the root separators (or the keys of a small bin) and
-// the tree shape into the header.  The warp's writes of the leaf run must be
-// visible to all its lanes (a __syncwarp after writing them is enough).
-template <typename KT>
-__device__ __forceinline__ void index_bin(void *store, BinHdr *hdr, int64_t g, int lane)
+// Index one bin whose sorted keys sit in its leaf run (W >= 8 lanes of a
+// warp, lane = 0..W-1 among them, mask = their bits; by default the whole
+// warp): pad the last leaf, fill the internal levels with the largest key
+// under each child, and write the root separators (or the keys of a small
+// bin) and the tree shape into the header.  The lanes' writes of the leaf
+// run must be visible to all of them (a __syncwarp(mask) after writing them
+// is enough).
+template <typename KT, int W = 32>
+__device__ __forceinline__ void index_bin(void *store, BinHdr *hdr, int64_t g, int lane,
+                                          unsigned mask = 0xffffffffu)
 {
+    static_assert(W >= 8 && W <= 32, "index_bin needs 8 to 32 lanes");
     constexpr int LK = KeyT<KT>::LK;
     constexpr int R = KeyT<KT>::R;
     {
@@ -172,11 +176,11 @@ __device__ __forceinline__ void index_bin(void *store, BinHdr *hdr, int64_t g, i
         const int h = run_levels(L0, LK, R);
         const uint32_t internal = internal_nodes(n, LK, R);
         KT *leaves = run + ((size_t)internal << LK);
-        for (uint32_t i = n + lane; i < (L0 << LK); i += 32) leaves[i] = pad_key<KT>();
+        for (uint32_t i = n + lane; i < (L0 << LK); i += W) leaves[i] = pad_key<KT>();
         uint32_t loff = 0;
         for (int l = h; l >= 1; --l) {
             const uint32_t cnt = level_count(L0, LK, l);
-            for (uint32_t slot = lane; slot < (cnt << LK); slot += 32) {
+            for (uint32_t slot = lane; slot < (cnt << LK); slot += W) {
                 const uint64_t first = (uint64_t)slot << (LK * l);
                 KT v = pad_key<KT>();
                 if (first < n) {
@@ -207,7 +211,7 @@ __device__ __forceinline__ void index_bin(void *store, BinHdr *hdr, int64_t g, i
             }
             hdr[g].w[lane] = word;
         }
-        __syncwarp();
+        __syncwarp(mask);
         if (lane == 0) hdr[g].nm = n | ((uint32_t)h << 24) | (level_count(L0, LK, h) << 28);
     }
 }

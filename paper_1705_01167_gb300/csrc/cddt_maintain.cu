@@ -400,6 +400,14 @@ __device__ __forceinline__ uint16_t shfl_key(uint16_t v, int k)
 {
     return (uint16_t)__shfl_sync(0xffffffffu, (uint32_t)v, k);
 }
+// The same within groups of W lanes (mask = the group's lanes).
+template <int W>
+__device__ __forceinline__ float shfl_key_w(unsigned mask, float v, int k) { return __shfl_sync(mask, v, k, W); }
+template <int W>
+__device__ __forceinline__ uint16_t shfl_key_w(unsigned mask, uint16_t v, int k)
+{
+    return (uint16_t)__shfl_sync(mask, (uint32_t)v, k, W);
+}
 
 // After the per-bin sort of the deltas: for every insert, the number of old
 // keys below it (lower_bound in its bin); for every delete, the index of the
@@ -620,17 +628,181 @@ __device__ __forceinline__ void merge_bin(const void *old_store, const BinHdr *o
 }
 
 
-// One warp per bin: merge, then index the new run (its keys were just
-// written by this warp and are read back from L2, not HBM).
+// Lanes per bin of the light merge (two bins per warp: the per-bin work of
+// reading the bin's sizes and offsets and indexing its new run is shared by
+// two bins, and 16 lanes x 8 keys cover the few hundred keys of a bin in one
+// or a few passes).
+constexpr int kMergeLanes = 16;
+
+// What a light merge reads about its bin before touching keys.
+struct LightBin {
+    uint32_t ni, nd;    // inserts, deletes
+    uint32_t ooff, on;  // old run: first node, keys
+    uint32_t noff, nn;  // new run
+    uint32_t io, dof;   // first insert, first delete
+};
+
+__device__ __forceinline__ LightBin light_bin_load(const BinHdr *old_hdr, const BinHdr *new_hdr,
+                                                   const uint32_t *ins_off, const uint32_t *ins_n,
+                                                   const uint32_t *del_off, const uint32_t *del_n, int64_t g)
+{
+    LightBin b;
+    b.ni = ins_n[g];
+    b.nd = del_n[g];
+    const uint2 o = *reinterpret_cast<const uint2 *>(old_hdr + g), w = *reinterpret_cast<const uint2 *>(new_hdr + g);
+    b.ooff = o.x;
+    b.on = bin_count(o.y);
+    b.noff = w.x;
+    b.nn = bin_count(w.y);
+    b.io = ins_off[g];
+    b.dof = del_off[g];
+    return b;
+}
+
+// Merge of a bin with at most 32 inserts and at most 32 deletes (nearly
+// every bin of an update), in the old run's index space only: insert j
+// precedes old key i iff its lower bound lb_j <= i, delete k removes old key
+// pos_k, so a kept old key i lands at i + #(lb_j <= i) - #(pos_k < i) and
+// insert j at lb_j + (its rank among the inserts) - #(pos_k < lb_j).  W
+// lanes of a warp serve the bin (lane = 0..W-1 among them, mask = their
+// bits); lane L holds old keys i0 + L + W e (e < 8), so that the loads and
+// stores of the lanes touch consecutive keys.  Each delta adds one to a byte
+// counter of the first e it covers, and one multiply by 0x0101..01 turns the
+// eight byte counters into their prefix sums (at most 32 per byte, no
+// carries).  The deltas are read W at a time and broadcast by shuffles.
+template <typename KT, int W>
+__device__ __forceinline__ void merge_bin_light(const void *old_store, void *new_store, const KT *ins_keys,
+                                                const int32_t *ins_lb, const int32_t *del_pos, const LightBin &b,
+                                                int lane, unsigned mask, int *status)
+{
+    const KT *old = leaf_run<KT>(const_cast<void *>(old_store), b.ooff, b.on);
+    KT *dst = leaf_run<KT>(new_store, b.noff, b.nn);
+    const int n = (int)b.on, ni = (int)b.ni, nd = (int)b.nd, nn = (int)b.nn;
+    const uint32_t io = b.io, dof = b.dof;
+    // Every delete must name a distinct old key (the locate pass flags one
+    // that does not and gives it position 0x7fffffff) and the new size must
+    // be n + ni - nd; then the positions below are a bijection onto [0, nn)
+    // and need no further checks.  A bin that breaks this is flagged and
+    // left unwritten.
+    bool bad = nd > n || nn != n + ni - nd;
+    for (int k0 = 0; k0 < nd; k0 += W)
+        bad |= k0 + lane < nd && (uint32_t)del_pos[dof + k0 + lane] >= (uint32_t)n;
+    if (__any_sync(mask, bad)) {
+        if (lane == 0) flag_error(status);
+        return;
+    }
+    if (ni == 0 && nd == 0) {
+        constexpr int V = 16 / (int)sizeof(KT);  // whole 16-byte pieces lie inside the padded run
+        for (int i = lane * V; i < n; i += W * V)
+            *reinterpret_cast<uint4 *>(dst + i) = __ldg(reinterpret_cast<const uint4 *>(old + i));
+        return;
+    }
+    constexpr int E = 8;
+    constexpr unsigned long long kOnes = 0x0101010101010101ull;
+    for (int i0 = 0; i0 < n; i0 += W * E) {
+        const int base = i0 + lane;  // this lane's key e = 0
+        const KT *src = old + base;
+        KT v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = base + W * e < n ? src[W * e] : KT(0);
+        unsigned long long ih = 0, dh = 0;
+        uint32_t gone = 0;
+        for (int k0 = 0; k0 < ni; k0 += W) {
+            const int lb = k0 + lane < ni ? ins_lb[io + k0 + lane] : 0;
+            const int m = min(W, ni - k0);
+            for (int k = 0; k < m; ++k) {
+                const int t = __shfl_sync(mask, lb, k, W) - base;  // keys >= lb: e >= ceil(t / W)
+                const int et = t <= 0 ? 0 : (t + W - 1) / W;
+                if (et < E) ih += 1ull << (8 * et);
+            }
+        }
+        for (int k0 = 0; k0 < nd; k0 += W) {
+            const int dp = k0 + lane < nd ? del_pos[dof + k0 + lane] : 0;
+            const int m = min(W, nd - k0);
+            for (int k = 0; k < m; ++k) {
+                const int t = __shfl_sync(mask, dp, k, W) - base;  // keys > pos: e >= ceil((t + 1) / W)
+                const int et = t < 0 ? 0 : (t + W) / W;
+                if (et < E) dh += 1ull << (8 * et);
+                if (t >= 0 && t % W == 0 && t < W * E) gone |= 1u << (t / W);
+            }
+        }
+        // byte e of sh: 64 + inserts before key e - deletes before it (each
+        // prefix sum is at most 32, so no byte borrows from its neighbour)
+        const unsigned long long sh = ih * kOnes + 0x4040404040404040ull - dh * kOnes;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (base + W * e < n && !((gone >> e) & 1u))
+                dst[base + W * e + (int)((sh >> (8 * e)) & 0xffu) - 64] = v[e];
+    }
+    // inserts: lb + rank among the inserts (equal keys in index order) -
+    // deletes below it; insert j is taken by lane j mod W
+    for (int j0 = 0; j0 < ni; j0 += W) {
+        const bool mine = j0 + lane < ni;
+        const KT ik = mine ? ins_keys[io + j0 + lane] : KT(0);
+        const int ilb = mine ? ins_lb[io + j0 + lane] : 0;
+        int r = ilb;
+        for (int k0 = 0; k0 < ni; k0 += W) {
+            const KT uk_l = k0 + lane < ni ? ins_keys[io + k0 + lane] : KT(0);
+            const int m = min(W, ni - k0);
+            for (int k = 0; k < m; ++k) {
+                const KT uk = shfl_key_w<W>(mask, uk_l, k);
+                r += (uk < ik) || (uk == ik && k0 + k < j0 + lane);
+            }
+        }
+        for (int k0 = 0; k0 < nd; k0 += W) {
+            const int dp = k0 + lane < nd ? del_pos[dof + k0 + lane] : 0;
+            const int m = min(W, nd - k0);
+            for (int k = 0; k < m; ++k) r -= __shfl_sync(mask, dp, k, W) < ilb;
+        }
+        if (mine) dst[r] = ik;
+    }
+}
+
+// A bin takes the light merge when it has at most 32 inserts and at most 32
+// deletes (the segmented sort leaves exactly those delta lists unsorted).
+__device__ __forceinline__ bool light_bin(uint32_t ni, uint32_t nd) { return ni <= 32 && nd <= 32; }
+
+// W lanes per light bin (32 / W bins per warp): merge, then index the new
+// run (its keys were just written by these lanes and are read back from L2,
+// not HBM).  Heavy bins are listed for upd_merge_kernel.
+template <typename KT, int W>
+__global__ void __launch_bounds__(256, 5) upd_merge_light_kernel(const void *old_store, const BinHdr *old_hdr,
+                                                                 void *new_store, BinHdr *new_hdr, const KT *ins_keys,
+                                                                 const uint32_t *ins_off, const uint32_t *ins_n,
+                                                                 const uint32_t *del_off, const uint32_t *del_n,
+                                                                 const int32_t *ins_lb, const int32_t *del_pos,
+                                                                 int64_t nbins, uint32_t *heavy, uint32_t *n_heavy,
+                                                                 int *status)
+{
+    const int lane = threadIdx.x & (W - 1);
+    const unsigned mask = W == 32 ? 0xffffffffu : ((1u << W) - 1u) << (threadIdx.x & 31 & ~(W - 1));
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W; g < nbins;
+         g += ((int64_t)gridDim.x * blockDim.x) / W) {
+        const LightBin b = light_bin_load(old_hdr, new_hdr, ins_off, ins_n, del_off, del_n, g);
+        if (!light_bin(b.ni, b.nd)) {  // left to upd_merge_kernel
+            if (lane == 0) heavy[atomicAdd(n_heavy, 1u)] = (uint32_t)g;
+            continue;
+        }
+        merge_bin_light<KT, W>(old_store, new_store, ins_keys, ins_lb, del_pos, b, lane, mask, status);
+        __syncwarp(mask);
+        index_bin<KT, W>(new_store, new_hdr, g, lane, mask);
+    }
+}
+
+// The other bins (more than 32 inserts or deletes; sorted delta lists), the
+// n_heavy of them that upd_merge_light_kernel listed, one warp per bin,
+// merged by merge_bin.
 template <typename KT>
 __global__ void __launch_bounds__(256, 4) upd_merge_kernel(const void *old_store, const BinHdr *old_hdr, void *new_store, BinHdr *new_hdr,
                                  const KT *ins_keys, const uint32_t *ins_off, const uint32_t *ins_n, const KT *del_keys,
                                  const uint32_t *del_off, const uint32_t *del_n, const int32_t *ins_lb,
-                                 const int32_t *del_pos, int64_t nbins, int *status)
+                                 const int32_t *del_pos, const uint32_t *heavy, const uint32_t *n_heavy, int *status)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nbins;
-         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t nh = *n_heavy;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nh;
+         t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t g = heavy[t];
         merge_bin<KT>(old_store, old_hdr, new_store, new_hdr, ins_keys, ins_off, ins_n, del_keys, del_off, del_n,
                       ins_lb, del_pos, g, lane, status);
         __syncwarp();
@@ -676,7 +848,8 @@ static cddt_status update_kt(cddt_s *h, const int32_t *xy, const uint8_t *occ, i
     size_t bytes = Arena::need(4 * (size_t)n) + Arena::need(36 * (size_t)n) + Arena::need(8) +
                    Arena::need(20 * nbz) + Arena::need(8 * sse) + Arena::need(16) + Arena::need(8 * nbz) +
                    Arena::need(sizeof(BinHdr) * nbz) + 2 * (Arena::need(4 * 8 * nbz) + Arena::need(4 * 8)) +
-                   Arena::need(4 * nbz) + 2 * Arena::need(8 * sse) + Arena::need(24);
+                   Arena::need(4 * nbz) + 2 * Arena::need(8 * sse) + Arena::need(24) + Arena::need(4 * nbz) +
+                   Arena::need(16);
     CDDT_TRY(reserve(&h->ws, &h->ws_bytes, bytes));
     Arena ws{reinterpret_cast<char *>(h->ws), h->ws_bytes, 0};
     uint32_t *changed = ws.take<uint32_t>((size_t)n), *flips = ws.take<uint32_t>(9 * (size_t)n);
@@ -685,7 +858,9 @@ static cddt_status update_kt(cddt_s *h, const int32_t *xy, const uint8_t *occ, i
     uint64_t *scratch = ws.take<uint64_t>(sse), *tot = ws.take<uint64_t>(2);
     uint32_t *cur = ws.take<uint32_t>(2 * nbz);
     BinHdr *old_hdr = ws.take<BinHdr>(nbz);
-    if (!changed || !flips || !nchanged || !arr || !scratch || !tot || !cur || !old_hdr) return CDDT_ERR_OOM;
+    uint32_t *heavy = ws.take<uint32_t>(nbz), *n_heavy = ws.take<uint32_t>(4);
+    if (!changed || !flips || !nchanged || !arr || !scratch || !tot || !cur || !old_hdr || !heavy || !n_heavy)
+        return CDDT_ERR_OOM;
     CDDT_CUDA(cudaMemsetAsync(nchanged, 0, sizeof(uint32_t) * 2, st));
     const unsigned gn = grid_cap(n, 256);
     upd_dedupe_kernel<<<gn, 256, 0, st>>>(xy, n, h->W, h->H, h->last_writer, h->status);
@@ -745,9 +920,13 @@ static cddt_status update_kt(cddt_s *h, const int32_t *xy, const uint8_t *occ, i
         return rc;
     }
     const int64_t store_cap = h->spare_nodes;
-    upd_merge_kernel<KT><<<grid_cap(nb * 32, 256), 256, 0, st>>>(h->store, old_hdr, store, h->hdr, ins_keys, ins_off,
-                                                                 ins_n, del_keys, del_off, del_n, ins_lb, del_pos, nb,
-                                                                 h->status);
+    CDDT_CUDA(cudaMemsetAsync(n_heavy, 0, sizeof(uint32_t), st));
+    upd_merge_light_kernel<KT, kMergeLanes><<<grid_cap(nb * kMergeLanes, 256), 256, 0, st>>>(
+        h->store, old_hdr, store, h->hdr, ins_keys, ins_off, ins_n, del_off, del_n, ins_lb, del_pos, nb, heavy, n_heavy,
+        h->status);
+    upd_merge_kernel<KT><<<sm_count() * 4, 256, 0, st>>>(h->store, old_hdr, store, h->hdr, ins_keys, ins_off, ins_n,
+                                                        del_keys, del_off, del_n, ins_lb, del_pos, heavy, n_heavy,
+                                                        h->status);
     CDDT_CUDA(cudaGetLastError());
     // the old store becomes the next update's target (stream order keeps the
     // merge's reads of it before any later write)
