@@ -43,62 +43,125 @@ __device__ __forceinline__ uint32_t raw_key(const KT *leaves, int i)
     return (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(leaves) + i);
 }
 
+// Marks of one free cell in one bin its extent reaches (reading S8): every
+// key m in [lower_bound(xlo) - 1, upper_bound(xhi)], clamped to the bin,
+// whose forward or backward gap meets the cell's widened x' extent.
 template <typename KT>
-__global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t keep_n)
+__device__ __forceinline__ void prune_mark_cell(const MapView &m, uint32_t g, const BinHdr &bh, float X, float xlo,
+                                                float xhi, uint64_t pol, uint8_t *keep, int64_t keep_n)
 {
     constexpr int LK = KeyT<KT>::LK;
-    const uint64_t pol = policy_evict_last();
-    const int64_t cells = (int64_t)m.W * m.H;
-    const int64_t total = cells * m.S;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(t / cells);
-        const int64_t q = t - (int64_t)s * cells;
-        if (__ldg(m.grid + q)) continue;
-        const int j = (int)(q / m.W), i = (int)(q - (int64_t)j * m.W);
-        const SliceInfo si = *chk_slice(m, m.slices + s, (int)sizeof(SliceInfo));
-        float xr, yr;
-        project((float)i, (float)j, si.c, si.s, xr, yr);
-        const float h = half_extent(si.c, si.s);
-        int b0, b1;
-        if (s == 0) {
-            b0 = b1 = j + si.T;
-        } else {
-            const float lo = __fsub_rn(__fsub_rn(yr, h), eps), hi = __fadd_rn(__fadd_rn(yr, h), eps);
-            b0 = (int)ceilf(__fsub_rn(lo, 0.5f)) + si.T;
-            b1 = (int)floorf(__fadd_rn(hi, 0.5f)) + si.T;
-        }
-        b0 = max(b0, 0);
-        b1 = min(b1, si.nb - 1);
-        const float xlo = __fsub_rn(__fsub_rn(xr, h), eps), xhi = __fadd_rn(__fadd_rn(xr, h), eps);
-        for (int b = b0; b <= b1; ++b) {
-            const uint32_t g = si.sbase + (uint32_t)b;
-            const BinHdr bh = *chk_hdr(m, m.hdr + g, (int)sizeof(BinHdr));
-            const uint32_t bn = bin_count(bh.nm);
-            if (bn == 0) continue;
-            int kb;
-            const SearchResult sl = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, si.X, pol, kb);
-            const int l = sl.idx;  // first key >= xlo
-            // first key > xhi: the cell's x' extent is under two units wide,
-            // so it is usually within a few keys of l (the leaf just read)
-            const KT *leaves = leaf_run<KT>(const_cast<void *>(m.store), bh.off, bn);
-            const Cmp<KT, true> above(m, xhi, si.X);
-            int u = l;
-            if (u < (int)bn && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) {
-                ++u;
-                while (u < (int)bn && u < l + 8 && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0)))
-                    ++u;
-                if (u == l + 8) u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, si.X, pol, kb).idx;
-            }
-            const int m0 = max(l - 1, 0), m1 = min(u, (int)bn - 1);
-            const int64_t k0 = ((int64_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK;
+    const uint32_t bn = bin_count(bh.nm);
+    int kb;
+    const SearchResult sl = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, X, pol, kb);
+    const int l = sl.idx;  // first key >= xlo
+    // first key > xhi: the cell's x' extent is under two units wide, so it
+    // is usually within a few keys of l (the leaf just read)
+    const KT *leaves = leaf_run<KT>(const_cast<void *>(m.store), bh.off, bn);
+    const Cmp<KT, true> above(m, xhi, X);
+    int u = l;
+    if (u < (int)bn && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) {
+        ++u;
+        while (u < (int)bn && u < l + 8 && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) ++u;
+        if (u == l + 8) u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, X, pol, kb).idx;
+    }
+    const int m0 = max(l - 1, 0), m1 = min(u, (int)bn - 1);
+    const int64_t k0 = ((int64_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK;
 #if CDDT_CHECKED
-            if (m0 <= m1 && (k0 + m0 < 0 || k0 + m1 >= keep_n)) {
-                atomicCAS(m.status, 0, (int)CDDT_ERR_BOUNDS);
-                continue;
-            }
+    if (m0 <= m1 && (k0 + m0 < 0 || k0 + m1 >= keep_n)) {
+        atomicCAS(m.status, 0, (int)CDDT_ERR_BOUNDS);
+        return;
+    }
+#else
+    (void)keep_n;
 #endif
-            for (int mm = m0; mm <= m1; ++mm) keep[k0 + mm] = 1;
+    for (int mm = m0; mm <= m1; ++mm) keep[k0 + mm] = 1;
+}
+
+// Prune marks, bin by bin: one warp per bin (s, b).  The free cells whose
+// widened y' extent meets the bin lie in a strip along direction s; the
+// lanes take consecutive lines of the strip (columns when |cos| >= sin,
+// else rows), so that the warp's searches all run in one bin, whose header
+// and nodes stay in L1.  Each line holds a few candidate cells: those whose
+// y' lies in the bin's band widened by a margin (0.25) far above the float
+// rounding of the candidate arithmetic; every candidate then takes the
+// exact per-cell test of reading S8 (the bins b0..b1 of the cell, computed
+// with the same float operations as the oracle), so each (free cell, bin)
+// pair is marked exactly when the cell-by-cell rule marks it.
+template <typename KT>
+__global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t keep_n, int64_t total_bins)
+{
+    const uint64_t pol = policy_evict_last();
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total_bins; g += nwarps) {
+        int lo = 0, hi = m.S - 1;  // slice of bin g: the last s with sbase <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)__ldg(&m.slices[mid].sbase) <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const int s = lo;
+        const SliceInfo si = *chk_slice(m, m.slices + s, (int)sizeof(SliceInfo));
+        const BinHdr bh = *chk_hdr(m, m.hdr + g, (int)sizeof(BinHdr));
+        if (bin_count(bh.nm) == 0) continue;
+        const int b = (int)(g - si.sbase);
+        const float c = si.c, sn = si.s;
+        const float h = half_extent(c, sn);
+        // candidate band of y' = j c - i sn
+        const float bp = (float)(b - si.T);
+        const float ylo = bp - 0.5f - h - eps - 0.25f, yhi = bp + 0.5f + h + eps + 0.25f;
+        const bool cols = fabsf(c) >= sn;
+        const int L = cols ? m.W : m.H;
+        // lines whose candidate range meets the map (one line of margin)
+        float k_lo = 0.0f, k_hi = (float)(L - 1);
+        if (cols) {  // j in [(ylo + i sn) / c, (yhi + i sn) / c] (ends swapped for c < 0)
+            if (sn > 0.0f) {
+                const float hc = (float)(m.H - 1) * c;
+                if (c > 0.0f) { k_lo = -yhi / sn; k_hi = (hc - ylo) / sn; }
+                else { k_lo = (hc - yhi) / sn; k_hi = -ylo / sn; }
+            } else if (yhi < 0.0f || ylo > (float)(m.H - 1)) {
+                continue;  // slice 0: the band misses every row
+            }
+        } else {  // i in [(j c - yhi) / sn, (j c - ylo) / sn]
+            const float ws = (float)(m.W - 1) * sn;
+            if (c > 0.0f) { k_lo = ylo / c; k_hi = (ws + yhi) / c; }
+            else if (c < 0.0f) { k_lo = (ws + yhi) / c; k_hi = ylo / c; }
+            else if (ylo > 0.0f || ws + yhi < 0.0f) continue;
+        }
+        const int l0 = max(0, (int)floorf(fmaxf(k_lo, -1.0f)) - 1);
+        const int l1 = min(L - 1, (int)ceilf(fminf(k_hi, (float)L)) + 1);
+        const float inv = 1.0f / (cols ? c : sn);
+        for (int k = l0 + lane; k <= l1; k += 32) {
+            int a0, a1;  // cells of line k: rows (cols) or columns
+            if (cols) {
+                const float p = ((float)k * sn + ylo) * inv, q = ((float)k * sn + yhi) * inv;
+                a0 = max(0, (int)ceilf(fminf(p, q)));
+                a1 = min(m.H - 1, (int)floorf(fmaxf(p, q)));
+            } else {
+                const float p = ((float)k * c - yhi) * inv, q = ((float)k * c - ylo) * inv;
+                a0 = max(0, (int)ceilf(p));
+                a1 = min(m.W - 1, (int)floorf(q));
+            }
+            for (int a = a0; a <= a1; ++a) {
+                const int i = cols ? k : a, j = cols ? a : k;
+                if (__ldg(m.grid + (int64_t)j * m.W + i)) continue;
+                float xr, yr;
+                project((float)i, (float)j, c, sn, xr, yr);
+                int b0, b1;
+                if (s == 0) {
+                    b0 = b1 = j + si.T;
+                } else {
+                    const float clo = __fsub_rn(__fsub_rn(yr, h), eps), chi = __fadd_rn(__fadd_rn(yr, h), eps);
+                    b0 = (int)ceilf(__fsub_rn(clo, 0.5f)) + si.T;
+                    b1 = (int)floorf(__fadd_rn(chi, 0.5f)) + si.T;
+                }
+                b0 = max(b0, 0);
+                b1 = min(b1, si.nb - 1);
+                if (b < b0 || b > b1) continue;
+                const float xlo = __fsub_rn(__fsub_rn(xr, h), eps), xhi = __fadd_rn(__fadd_rn(xr, h), eps);
+                prune_mark_cell<KT>(m, (uint32_t)g, bh, si.X, xlo, xhi, pol, keep, keep_n);
+            }
         }
     }
 }
@@ -158,10 +221,8 @@ static cddt_status prune_kt(cddt_s *h, cudaStream_t st)
     CDDT_CUDA(cnt.alloc(sizeof(uint32_t) * (size_t)std::max<int64_t>(nb, 1)));
     CDDT_CUDA(old_hdr.alloc(sizeof(BinHdr) * (size_t)std::max<int64_t>(nb, 1)));
     CDDT_CUDA(cudaMemsetAsync(keep.p, 0, (size_t)h->store_nodes * K, st));
-    const int64_t work = (int64_t)h->W * h->H * h->S;
-    prune_mark_kernel<KT><<<grid_cap(work, 256, 32), 256, 0, st>>>(h->view(), prune_eps(h->W, h->H),
-                                                                          keep.as<uint8_t>(),
-                                                                          h->store_nodes * K);
+    prune_mark_kernel<KT><<<grid_cap(nb * 32, 256, 32), 256, 0, st>>>(h->view(), prune_eps(h->W, h->H),
+                                                                        keep.as<uint8_t>(), h->store_nodes * K, nb);
     count_kept_kernel<KT><<<grid_cap(nb * 32, 256), 256, 0, st>>>(h->hdr, nb, keep.as<uint8_t>(), cnt.as<uint32_t>());
     CDDT_CUDA(cudaMemcpyAsync(old_hdr.p, h->hdr, sizeof(BinHdr) * nb, cudaMemcpyDeviceToDevice, st));
     CDDT_CUDA(cudaGetLastError());
