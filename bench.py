@@ -662,7 +662,15 @@ def bench_corridor(args, G, torch, dev, world, rank):
     ms_u = timed(plan_u.run, k2, 2)
     ms_uu = timed(lambda: du.calc_range_many(sw, out=out), 5, 2)
     ms_ug = timed(lambda: du.calc_range_many(gq, out=gout), 3, 1)
+    # uniform particles (global localization) on the 16-bit store: there the
+    # gathers reach DRAM, and the store is half the size
+    plan_uq = G.Plan(filters_for(du, upart_d))
+    shape_uq = plan_uq.autotune()
+    ms_uq = timed(plan_uq.run, k2, 2)
+    plan_uq.close()
     extra["u16"] = {"rays_per_s": rays_per_step / (statistics.mean(ms_u) * 1e-3),
+                    "uniform_particles_rays_per_s": rays_per_step / (statistics.mean(ms_uq) * 1e-3),
+                    "uniform_particles_shape": shape_uq,
                     "sweep_rays_per_s": sw.shape[0] / (statistics.mean(ms_uu) * 1e-3),
                     "grid_sweep_rays_per_s": gq.shape[0] / (statistics.mean(ms_ug) * 1e-3),
                     "store_bytes": stu["store_bytes"], "f32_store_bytes": st0["store_bytes"],

@@ -45,19 +45,30 @@ __device__ __forceinline__ uint32_t raw_key(const KT *leaves, int i)
 
 // Marks of one free cell in one bin its extent reaches (reading S8): every
 // key m in [lower_bound(xlo) - 1, upper_bound(xhi)], clamped to the bin,
-// whose forward or backward gap meets the cell's widened x' extent.
+// whose forward or backward gap meets the cell's widened x' extent.  lc is
+// the lower bound found for the previous cell of the same line (-1: none):
+// the cells of a line lie within a unit of one another in x', so the bound
+// moves by a key or two from there instead of a new tree search.
 template <typename KT>
 __device__ __forceinline__ void prune_mark_cell(const MapView &m, uint32_t g, const BinHdr &bh, float X, float xlo,
-                                                float xhi, uint64_t pol, uint8_t *keep, int64_t keep_n)
+                                                float xhi, uint64_t pol, uint8_t *keep, int64_t keep_n, int &lc)
 {
     constexpr int LK = KeyT<KT>::LK;
     const uint32_t bn = bin_count(bh.nm);
+    const KT *leaves = leaf_run<KT>(const_cast<void *>(m.store), bh.off, bn);
     int kb;
-    const SearchResult sl = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, X, pol, kb);
-    const int l = sl.idx;  // first key >= xlo
+    int l;  // first key >= xlo
+    if (lc < 0) {
+        l = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, X, pol, kb).idx;
+    } else {
+        const Cmp<KT, false> below(m, xlo, X);  // key < xlo, as in the tree search
+        l = lc;
+        while (l > 0 && !below.le(raw_key<KT>(chk_store(m, leaves + l - 1, (int)sizeof(KT)), 0))) --l;
+        while (l < (int)bn && below.le(raw_key<KT>(chk_store(m, leaves + l, (int)sizeof(KT)), 0))) ++l;
+    }
+    lc = l;
     // first key > xhi: the cell's x' extent is under two units wide, so it
     // is usually within a few keys of l (the leaf just read)
-    const KT *leaves = leaf_run<KT>(const_cast<void *>(m.store), bh.off, bn);
     const Cmp<KT, true> above(m, xhi, X);
     int u = l;
     if (u < (int)bn && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) {
@@ -133,6 +144,7 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t k
         const int l1 = min(L - 1, (int)ceilf(fminf(k_hi, (float)L)) + 1);
         const float inv = 1.0f / (cols ? c : sn);
         for (int k = l0 + lane; k <= l1; k += 32) {
+            int lc = -1;
             int a0, a1;  // cells of line k: rows (cols) or columns
             if (cols) {
                 const float p = ((float)k * sn + ylo) * inv, q = ((float)k * sn + yhi) * inv;
@@ -160,7 +172,7 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t k
                 b1 = min(b1, si.nb - 1);
                 if (b < b0 || b > b1) continue;
                 const float xlo = __fsub_rn(__fsub_rn(xr, h), eps), xhi = __fadd_rn(__fadd_rn(xr, h), eps);
-                prune_mark_cell<KT>(m, (uint32_t)g, bh, si.X, xlo, xhi, pol, keep, keep_n);
+                prune_mark_cell<KT>(m, (uint32_t)g, bh, si.X, xlo, xhi, pol, keep, keep_n, lc);
             }
         }
     }
