@@ -1012,10 +1012,22 @@ def run_gpu(args):
 
 def run_profile_update(args):
     """A short run for ncu: build the 4000 x 4000 corridor CDDT, then apply
-    warmup + steps batches of 10^4 cell writes (the update4000 writes)."""
+    warmup + steps batches of 10^4 cell writes (the update4000 writes); with
+    --profile-case update2000 the 2000 x 2000 corridor CDDT (theta_disc 200)
+    and batches of 2,800 writes (1,400 set, 1,400 cleared), the same number
+    of changes per bin on a store that an ncu capture handles in seconds."""
     import torch
     from paper_1705_01167_gb300 import cddt as G
-    w = WL.update4000(steps=args.warmup + args.steps)
+    if args.profile_case == "update2000":
+        g = synth.corridor_map(2000, 2000)
+        cur, writes = g.copy(), []
+        for t in range(args.warmup + args.steps):
+            xy, occ = synth.cell_toggles(cur, 1400, 1400, seed=synth.SEED_UPDATES + t)
+            writes.append((xy, occ))
+            cur = synth.apply_writes(cur, xy, occ)
+        w = dict(grid=g, theta_disc=200, max_range=1000.0, writes=writes)
+    else:
+        w = WL.update4000(steps=args.warmup + args.steps)
     dev = torch.device("cuda", 0)
     d = G.CDDT(torch.from_numpy(w["grid"]).to(dev), w["theta_disc"], w["max_range"])
     ms = []
@@ -1025,6 +1037,25 @@ def run_profile_update(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile": "update", "update_ms": ms, "status": d.status(),
                       "zero_points": d.stats()["n_zero_points"]}))
+    return 0
+
+
+def run_profile_prune(args):
+    """A short run for ncu: build the 2000 x 2000 corridor CDDT (theta_disc
+    200) and prune it, warmup + steps times (a fresh handle each time)."""
+    import torch
+    from paper_1705_01167_gb300 import cddt as G
+    dev = torch.device("cuda", 0)
+    grid = torch.from_numpy(synth.corridor_map(2000, 2000)).to(dev)
+    ms = []
+    for _ in range(args.warmup + args.steps):
+        d = G.CDDT(grid, 200, 1000.0)
+        d.prune()
+        st = d.stats()
+        ms.append(round(st["prune_ms"], 3))
+        d.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "prune", "prune_ms": ms, "zero_points": st["n_zero_points"]}))
     return 0
 
 
@@ -1076,8 +1107,10 @@ def run_profile_sweep4000(args):
 def run_profile(args):
     """A short run for ncu: the batched launch (fixed shape), one per-filter
     pass and one sweep launch, a few launches each."""
-    if args.profile_case == "update":
+    if args.profile_case in ("update", "update2000"):
         return run_profile_update(args)
+    if args.profile_case == "prune":
+        return run_profile_prune(args)
     if args.profile_case == "sweep4000":
         return run_profile_sweep4000(args)
     if args.profile_case == "refine":
@@ -1131,9 +1164,11 @@ def main():
                     help="default workload only: skip the other configurations' compact measurements")
     ap.add_argument("--config-steps", type=int, default=10, help="timed steps of each other configuration")
     ap.add_argument("--profile", action="store_true", help="short fixed-shape run for ncu")
-    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "u16", "uniform", "update", "refine", "sweep4000"],
+    ap.add_argument("--profile-case", default="corridor", choices=["corridor", "u16", "uniform", "update", "update2000", "prune", "refine",
+                             "sweep4000"],
                     help="--profile workload: the corridor plan (u16: on the 16-bit store; uniform: uniform "
-                         "particles), 10^4-write updates on the 4000^2 map, the diff2000 refinement launch, "
+                         "particles), 10^4-write updates on the 4000^2 map (update2000: 2,800-write updates on the "
+                         "2000^2 map), pruning the 2000^2 map, the diff2000 refinement launch, "
                          "or a 10 M sweep of the 4000^2 map, unsorted and slice-sorted")
     ap.add_argument("--shape-tpp", type=int, default=1)
     ap.add_argument("--shape-ppi", type=int, default=512)

@@ -45,48 +45,34 @@ __device__ __forceinline__ uint32_t raw_key(const KT *leaves, int i)
 
 // Marks of one free cell in one bin its extent reaches (reading S8): every
 // key m in [lower_bound(xlo) - 1, upper_bound(xhi)], clamped to the bin,
-// whose forward or backward gap meets the cell's widened x' extent.  lc is
-// the lower bound found for the previous cell of the same line (-1: none):
-// the cells of a line lie within a unit of one another in x', so the bound
-// moves by a key or two from there instead of a new tree search.
+// whose forward or backward gap meets the cell's widened x' extent.  The
+// bin's leaf run (leaves, bn keys) and its marks (kp) come from the caller;
+// lc holds a lower bound near the cell's (the search of its line), which
+// moves by a key or two to the cell's own: the cells of a line lie within
+// a unit of one another in x'.
 template <typename KT>
-__device__ __forceinline__ void prune_mark_cell(const MapView &m, uint32_t g, const BinHdr &bh, float X, float xlo,
-                                                float xhi, uint64_t pol, uint8_t *keep, int64_t keep_n, int &lc)
+__device__ __forceinline__ void prune_mark_cell(const MapView &m, uint32_t g, float X, float xlo, float xhi,
+                                                uint64_t pol, const KT *leaves, int bn, uint8_t *kp, int &lc)
 {
-    constexpr int LK = KeyT<KT>::LK;
-    const uint32_t bn = bin_count(bh.nm);
-    const KT *leaves = leaf_run<KT>(const_cast<void *>(m.store), bh.off, bn);
-    int kb;
-    int l;  // first key >= xlo
-    if (lc < 0) {
-        l = bin_search<KT, false, CDDT_SEARCH_TREE>(m, g, xlo, X, pol, kb).idx;
-    } else {
-        const Cmp<KT, false> below(m, xlo, X);  // key < xlo, as in the tree search
-        l = lc;
-        while (l > 0 && !below.le(raw_key<KT>(chk_store(m, leaves + l - 1, (int)sizeof(KT)), 0))) --l;
-        while (l < (int)bn && below.le(raw_key<KT>(chk_store(m, leaves + l, (int)sizeof(KT)), 0))) ++l;
-    }
-    lc = l;
+    const Cmp<KT, false> below(m, xlo, X);  // key < xlo, as in the tree search
+    int l = lc;
+    while (l > 0 && !below.le(raw_key<KT>(chk_store(m, leaves + l - 1, (int)sizeof(KT)), 0))) --l;
+    while (l < bn && below.le(raw_key<KT>(chk_store(m, leaves + l, (int)sizeof(KT)), 0))) ++l;
+    lc = l;  // first key >= xlo
     // first key > xhi: the cell's x' extent is under two units wide, so it
-    // is usually within a few keys of l (the leaf just read)
+    // is usually within a few keys of l
     const Cmp<KT, true> above(m, xhi, X);
     int u = l;
-    if (u < (int)bn && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) {
+    if (u < bn && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) {
         ++u;
-        while (u < (int)bn && u < l + 8 && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) ++u;
-        if (u == l + 8) u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, X, pol, kb).idx;
+        while (u < bn && u < l + 8 && above.le(raw_key<KT>(chk_store(m, leaves + u, (int)sizeof(KT)), 0))) ++u;
+        if (u == l + 8) {
+            int kb;
+            u = bin_search<KT, true, CDDT_SEARCH_TREE>(m, g, xhi, X, pol, kb).idx;
+        }
     }
-    const int m0 = max(l - 1, 0), m1 = min(u, (int)bn - 1);
-    const int64_t k0 = ((int64_t)bh.off + internal_nodes(bn, LK, KeyT<KT>::R)) << LK;
-#if CDDT_CHECKED
-    if (m0 <= m1 && (k0 + m0 < 0 || k0 + m1 >= keep_n)) {
-        atomicCAS(m.status, 0, (int)CDDT_ERR_BOUNDS);
-        return;
-    }
-#else
-    (void)keep_n;
-#endif
-    for (int mm = m0; mm <= m1; ++mm) keep[k0 + mm] = 1;
+    const int m1 = min(u, bn - 1);
+    for (int mm = max(l - 1, 0); mm <= m1; ++mm) kp[mm] = 1;
 }
 
 // Prune marks, bin by bin: one warp per bin (s, b).  The free cells whose
@@ -98,10 +84,13 @@ __device__ __forceinline__ void prune_mark_cell(const MapView &m, uint32_t g, co
 // rounding of the candidate arithmetic; every candidate then takes the
 // exact per-cell test of reading S8 (the bins b0..b1 of the cell, computed
 // with the same float operations as the oracle), so each (free cell, bin)
-// pair is marked exactly when the cell-by-cell rule marks it.
+// pair is marked exactly when the cell-by-cell rule marks it.  A line
+// takes one tree search (at its first candidate's x') and its cells move
+// from there.
 template <typename KT>
 __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t keep_n, int64_t total_bins)
 {
+    constexpr int LK = KeyT<KT>::LK;
     const uint64_t pol = policy_evict_last();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -115,7 +104,19 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t k
         const int s = lo;
         const SliceInfo si = *chk_slice(m, m.slices + s, (int)sizeof(SliceInfo));
         const BinHdr bh = *chk_hdr(m, m.hdr + g, (int)sizeof(BinHdr));
-        if (bin_count(bh.nm) == 0) continue;
+        const int bn = (int)bin_count(bh.nm);
+        if (bn == 0) continue;
+        const int64_t k0 = ((int64_t)bh.off + internal_nodes((uint32_t)bn, LK, KeyT<KT>::R)) << LK;
+#if CDDT_CHECKED
+        if (k0 < 0 || k0 + bn > keep_n) {
+            atomicCAS(m.status, 0, (int)CDDT_ERR_BOUNDS);
+            continue;
+        }
+#else
+        (void)keep_n;
+#endif
+        const KT *leaves = reinterpret_cast<const KT *>(m.store) + k0;
+        uint8_t *kp = keep + k0;
         const int b = (int)(g - si.sbase);
         const float c = si.c, sn = si.s;
         const float h = half_extent(c, sn);
@@ -144,7 +145,6 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t k
         const int l1 = min(L - 1, (int)ceilf(fminf(k_hi, (float)L)) + 1);
         const float inv = 1.0f / (cols ? c : sn);
         for (int k = l0 + lane; k <= l1; k += 32) {
-            int lc = -1;
             int a0, a1;  // cells of line k: rows (cols) or columns
             if (cols) {
                 const float p = ((float)k * sn + ylo) * inv, q = ((float)k * sn + yhi) * inv;
@@ -154,6 +154,14 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t k
                 const float p = ((float)k * c - yhi) * inv, q = ((float)k * c - ylo) * inv;
                 a0 = max(0, (int)ceilf(p));
                 a1 = min(m.W - 1, (int)floorf(q));
+            }
+            int lc = 0;
+            if (a0 <= a1) {  // the line's search, at its first candidate
+                float xr, yr;
+                project((float)(cols ? k : a0), (float)(cols ? a0 : k), c, sn, xr, yr);
+                int kb;
+                lc = bin_search<KT, false, CDDT_SEARCH_TREE>(m, (uint32_t)g, __fsub_rn(__fsub_rn(xr, h), eps), si.X,
+                                                             pol, kb).idx;
             }
             for (int a = a0; a <= a1; ++a) {
                 const int i = cols ? k : a, j = cols ? a : k;
@@ -172,7 +180,7 @@ __global__ void prune_mark_kernel(MapView m, float eps, uint8_t *keep, int64_t k
                 b1 = min(b1, si.nb - 1);
                 if (b < b0 || b > b1) continue;
                 const float xlo = __fsub_rn(__fsub_rn(xr, h), eps), xhi = __fadd_rn(__fadd_rn(xr, h), eps);
-                prune_mark_cell<KT>(m, (uint32_t)g, bh, si.X, xlo, xhi, pol, keep, keep_n, lc);
+                prune_mark_cell<KT>(m, (uint32_t)g, si.X, xlo, xhi, pol, leaves, bn, kp, lc);
             }
         }
     }

@@ -154,6 +154,36 @@ def test_update_bin_with_many_deltas(G, oracle, u16):
     assert bits_equal(d.calc_range_many(dev(q)).cpu().numpy(), ref.calc_range(q))
 
 
+@pytest.mark.parametrize("u16", [False, True])
+def test_update_light_heavy_boundary(G, oracle, u16):
+    """Bins at the edge between the two merges: a one-cell wall of 32 cells
+    along a row gives that row's slice-0 bin exactly 32 inserts (the light
+    merge's limit), one of 33 cells 33 (the sorted merge); then one update
+    clears the 32-cell wall and draws another 32 cells in the same row (32
+    deletes and 32 inserts in one bin), and the 33-cell wall is cleared."""
+    g = np.zeros((64, 512), np.uint8)
+    g[0, :] = g[-1, :] = 1
+    g[:, 0] = g[:, -1] = 1
+    N, mr = 40, 600.0
+    d = G.CDDT(dev(g), N, mr, u16=u16)
+    cur = g.copy()
+    a = np.array([(x, 20) for x in range(100, 132)], np.int32)
+    b = np.array([(x, 40) for x in range(200, 233)], np.int32)
+    c = np.array([(x, 20) for x in range(300, 332)], np.int32)
+    steps = ((np.concatenate([a, b]), np.ones(len(a) + len(b), np.uint8)),
+             (np.concatenate([a, c, b]), np.concatenate([np.zeros(len(a), np.uint8), np.ones(len(c), np.uint8),
+                                                         np.zeros(len(b), np.uint8)])))
+    for xy, occ in steps:
+        d.update_cells(dev(xy), dev(occ))
+        assert d.status() == G.CDDT_OK
+        for (x, y), v in zip(xy, occ):
+            cur[y, x] = v
+        same_store(d, oracle.OracleCDDT(cur, N, mr, u16=u16))
+    q = gc.random_queries(512, 64, 20000, 7)
+    ref = oracle.OracleCDDT(cur, N, mr, u16=u16)
+    assert bits_equal(d.calc_range_many(dev(q)).cpu().numpy(), ref.calc_range(q))
+
+
 def test_update_repeated_cells_last_write_wins(G, oracle):
     g = synth.rect_map(64, 64, n_rects=6, seed=5)
     d = G.CDDT(dev(g), 24, 100.0)
