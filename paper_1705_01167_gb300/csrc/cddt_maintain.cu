@@ -481,6 +481,15 @@ __device__ __forceinline__ uint16_t shfl_key(uint16_t v, int k)
 {
     return (uint16_t)__shfl_sync(0xffffffffu, (uint32_t)v, k);
 }
+// Ballot over a group of W lanes (mask = the group's lanes): bit k for the
+// group's lane k.
+template <int W>
+__device__ __forceinline__ uint32_t group_ballot(unsigned mask, bool p)
+{
+    const uint32_t b = __ballot_sync(mask, p);
+    if (W == 32) return b;
+    return (b >> (threadIdx.x & 31 & ~(W - 1))) & ((1u << W) - 1u);
+}
 // The same within groups of W lanes (mask = the group's lanes).
 template <int W>
 __device__ __forceinline__ float shfl_key_w(unsigned mask, float v, int k) { return __shfl_sync(mask, v, k, W); }
@@ -786,22 +795,27 @@ __device__ __forceinline__ void merge_bin_light(const void *old_store, void *new
         KT v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = base + W * e < n ? src[W * e] : KT(0);
+        // changes before this pass shift every key of it alike (a count in
+        // byte 0); only those inside it are placed key slot by key slot
+        const int iend = i0 + W * E;
         unsigned long long ih = 0, dh = 0;
         uint32_t gone = 0;
         for (int k0 = 0; k0 < ni; k0 += W) {
-            const int lb = k0 + lane < ni ? ins_lb[io + k0 + lane] : 0;
-            const int m = min(W, ni - k0);
-            for (int k = 0; k < m; ++k) {
-                const int t = __shfl_sync(mask, lb, k, W) - base;  // keys >= lb: e >= ceil(t / W)
+            const bool v = k0 + lane < ni;
+            const int lb = v ? ins_lb[io + k0 + lane] : 0;
+            ih += (unsigned)__popc(group_ballot<W>(mask, v && lb < i0));
+            for (uint32_t in = group_ballot<W>(mask, v && lb >= i0 && lb < iend); in; in &= in - 1) {
+                const int t = __shfl_sync(mask, lb, __ffs(in) - 1, W) - base;  // keys >= lb: e >= ceil(t / W)
                 const int et = t <= 0 ? 0 : (t + W - 1) / W;
                 if (et < E) ih += 1ull << (8 * et);
             }
         }
         for (int k0 = 0; k0 < nd; k0 += W) {
-            const int dp = k0 + lane < nd ? del_pos[dof + k0 + lane] : 0;
-            const int m = min(W, nd - k0);
-            for (int k = 0; k < m; ++k) {
-                const int t = __shfl_sync(mask, dp, k, W) - base;  // keys > pos: e >= ceil((t + 1) / W)
+            const bool v = k0 + lane < nd;
+            const int dp = v ? del_pos[dof + k0 + lane] : 0;
+            dh += (unsigned)__popc(group_ballot<W>(mask, v && dp < i0));
+            for (uint32_t in = group_ballot<W>(mask, v && dp >= i0 && dp < iend); in; in &= in - 1) {
+                const int t = __shfl_sync(mask, dp, __ffs(in) - 1, W) - base;  // keys > pos: e >= ceil((t + 1) / W)
                 const int et = t < 0 ? 0 : (t + W) / W;
                 if (et < E) dh += 1ull << (8 * et);
                 if (t >= 0 && t % W == 0 && t < W * E) gone |= 1u << (t / W);
