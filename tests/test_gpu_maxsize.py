@@ -53,3 +53,31 @@ def test_maximum_map_side(G, oracle, H, W):
     assert np.array_equal(bits(rm.calc_range_many(dev(q), steps=steps).cpu().numpy()), bits(want))
     assert np.array_equal(steps.cpu().numpy(), wsteps)
     assert np.array_equal(bits(d.cast_bresenham(dev(q)).cpu().numpy()), bits(O.cast_bresenham(g, q, mr)))
+
+
+@pytest.mark.parametrize("H, W", [(3, 32767), (32767, 3)])
+def test_maximum_map_side_prune_and_update(G, oracle, H, W):
+    """Pruning and a batch of cell writes on the largest maps: the
+    prune's strip enumeration and the update's merge at coordinates up to
+    32767, both bit-exact against the oracle's prune and update."""
+    rs = synth.Stream(79)
+    g = (rs.uniform(W * H) < 0.5).astype(np.uint8).reshape(H, W)  # dense: the prune drops ~2 % of the keys
+    N, mr = 36, 40000.0
+    q = np.concatenate([gc.special_queries(W, H), gc.random_queries(W, H, 20000, 80)])
+    xy, occ = synth.cell_toggles(g, 400, 400, seed=81)
+    for u16 in (False, True):
+        d = G.CDDT(dev(g), N, mr, u16=u16)
+        o = oracle.OracleCDDT(g, N, mr, u16=u16)
+        d.update_cells(dev(xy), dev(occ))
+        assert d.status() == G.CDDT_OK
+        assert o.update(xy, occ) == 0
+        _, bs, zp = d.export()
+        obs_, ozp = o.export()
+        assert np.array_equal(bs, obs_) and np.array_equal(bits(zp), bits(ozp)), ("update", u16)
+        d.prune()
+        o.prune()
+        _, bs, zp = d.export()
+        obs_, ozp = o.export()
+        assert np.array_equal(bs, obs_) and np.array_equal(bits(zp), bits(ozp)), ("prune", u16)
+        assert np.array_equal(bits(d.calc_range_many(dev(q)).cpu().numpy()), bits(o.calc_range(q))), u16
+        d.close()
