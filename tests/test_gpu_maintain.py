@@ -58,6 +58,27 @@ def test_prune_tiny_maps(G, oracle, u16):
             assert bits_equal(after, o.calc_range(q))
 
 
+@pytest.mark.parametrize("u16", [False, True])
+def test_prune_degenerate_maps(G, oracle, u16):
+    """Single cells, single rows and columns, all-free and all-occupied maps
+    (the prune's strips of one line or one cell), against the oracle's prune."""
+    rs = synth.Stream(91)
+    maps = [np.zeros((1, 1), np.uint8), np.ones((1, 1), np.uint8), np.zeros((4, 5), np.uint8),
+            np.ones((3, 4), np.uint8), (rs.uniform(9) < 0.4).astype(np.uint8).reshape(1, 9),
+            (rs.uniform(9) < 0.4).astype(np.uint8).reshape(9, 1),
+            (rs.uniform(6) < 0.5).astype(np.uint8).reshape(2, 3)]
+    for mi, g in enumerate(maps):
+        H, W = g.shape
+        for N in (4, 8, 36):
+            d = G.CDDT(dev(g), N, 20.0, u16=u16)
+            o = oracle.OracleCDDT(g, N, 20.0, u16=u16)
+            d.prune()
+            o.prune()
+            same_store(d, o)
+            q = gc.random_queries(W, H, 500, 100 + mi)
+            assert bits_equal(d.calc_range_many(dev(q)).cpu().numpy(), o.calc_range(q)), (mi, N)
+
+
 def _free_mask(g, q):
     H, W = g.shape
     fx = np.floor(q[:, 0] + np.float32(0.5))
