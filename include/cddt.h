@@ -280,8 +280,9 @@ CDDT_API cddt_status cddt_plan_run(cddt_plan p, void *stream);
  * must be set for every filter with P > 0; particles_out_dev may equal
  * particles_dev.  steps >= 0 (0: one forward + adjoint evaluation), eta >= 0,
  * tpp: lanes per particle, 0 to choose from the plan's size, else 1, 2, 4,
- * 8, 16 or 32 (results agree to float32 rounding of the per-particle sums
- * across tpp).  Safe to capture in a CUDA graph once it has run outside one
+ * 8, 16, 32, 64, 128 or 256 (above 32 a particle spans several warps of a
+ * block; results agree to float32 rounding of the per-particle sums across
+ * tpp).  Safe to capture in a CUDA graph once it has run outside one
  * with the same tpp (its work table is uploaded on first use).
  * Errors: ARG, CUDA. */
 CDDT_API cddt_status cddt_plan_refine(cddt_plan p, int32_t steps, float eta, int32_t tpp, void *stream);

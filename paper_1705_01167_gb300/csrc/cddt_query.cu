@@ -764,12 +764,12 @@ cddt_status plan_refine(cddt_plan_s *p, int32_t steps, float eta, int32_t tpp, c
         if (rc != CDDT_OK) return rc;
         rebuilt = true;
     }
-    if (tpp == 0) {  // lanes per particle: enough threads to fill the GPU
+    if (tpp == 0) {  // lanes per particle: two waves of resident threads (2048 per SM)
         int64_t total = 0;
         for (const cddt_filter &F : p->filters) total += std::max<int64_t>(F.P, 0);
-        const int64_t want = ((int64_t)sm_count() * 2048 + std::max<int64_t>(total, 1) - 1) / std::max<int64_t>(total, 1);
+        const int64_t want = ((int64_t)sm_count() * 4096 + std::max<int64_t>(total, 1) - 1) / std::max<int64_t>(total, 1);
         tpp = 1;
-        while (tpp < want && tpp < 32) tpp <<= 1;
+        while (tpp < want && tpp < kRefineBlock) tpp <<= 1;
     }
     if (rebuilt || p->refine_tpp != tpp || !p->refine_items_dev) {
         cddt_status rc = refine_items(p, tpp, st);
@@ -937,7 +937,9 @@ cddt_status cddt_plan_refine(cddt_plan p, int32_t steps, float eta, int32_t tpp,
     CDDT_RANGE("cddt_plan_refine", stream);
     if (!p) return CDDT_ERR_ARG;
     if (steps < 0 || !(eta >= 0.0f) || !(eta < 1e30f)) return CDDT_ERR_ARG;
-    if (!(tpp == 0 || tpp == 1 || tpp == 2 || tpp == 4 || tpp == 8 || tpp == 16 || tpp == 32)) return CDDT_ERR_ARG;
+    if (!(tpp == 0 || tpp == 1 || tpp == 2 || tpp == 4 || tpp == 8 || tpp == 16 || tpp == 32 || tpp == 64 ||
+          tpp == 128 || tpp == 256))
+        return CDDT_ERR_ARG;
     for (const cddt_filter &F : p->filters)
         if (F.P > 0 && (!F.grad_xy_dev || !F.particles_out_dev)) return CDDT_ERR_ARG;
     CDDT_FAULT_POINT("cddt_plan_refine");

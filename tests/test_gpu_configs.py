@@ -210,7 +210,8 @@ def test_corridor2000_plan_refinement(G, oracle):
     (cddt_plan_refine).  Every step is checked: the run of k steps ends at the
     pose of the run of k - 1 steps moved by that run's own gradient (bit for
     bit), and its log-weights and gradients match the float64 oracle at that
-    pose; lanes per particle 1, 8 and the automatic choice agree."""
+    pose; lanes per particle 1, 8, 128, 256 (a particle over several warps)
+    and the automatic choice agree."""
     w = WL.diff2000()
     o = oracle.OracleCDDT(w["grid"], w["theta_disc"], w["max_range"])
     d = G.CDDT(dev(w["grid"]), w["theta_disc"], w["max_range"])
@@ -227,7 +228,7 @@ def test_corridor2000_plan_refinement(G, oracle):
         host.append((sc, obs))
     plan = G.Plan(filters)
     eta = w["eta"]
-    for tpp in (0, 1, 8):
+    for tpp in (0, 1, 8, 128, 256):
         prev = None
         for k in range(w["refine_steps"] + 1 if tpp == 0 else 3):
             plan.refine(k, eta, tpp=tpp)
