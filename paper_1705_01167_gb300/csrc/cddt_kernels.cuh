@@ -136,6 +136,11 @@ cddt_status index_store(cddt_s *h, cudaStream_t st);
 // projected coordinate.
 float prune_eps(int W, int H);
 
+// Threads of a block of the gradient refinement kernels (cddt_plan_refine
+// launches them with this size; the wider kernels size their shared sums by
+// it).
+constexpr int kRefineBlock = 256;
+
 // Blocks of a grid-stride launch over n items: one per `threads` items, at
 // most per_sm blocks per streaming multiprocessor.
 inline unsigned grid_cap(int64_t n, int threads, int64_t per_sm = 64)

@@ -723,7 +723,6 @@ cddt_status plan_run(cddt_plan_s *p, cudaStream_t st)
 
 // Refinement items: the filters of every forward launch, cut into items of
 // kRefineBlock / tpp particles (one block's particles at once).
-constexpr int kRefineBlock = 256;
 static cddt_status refine_items(cddt_plan_s *p, int tpp, cudaStream_t st)
 {
     std::vector<WorkItem> items;

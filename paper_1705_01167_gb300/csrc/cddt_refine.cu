@@ -5,8 +5,6 @@
 
 namespace cddt {
 
-constexpr int kRefineThreads = 256;  // the block size cddt_plan_refine launches
-
 // refine_kernel for TPP = 64, 128 or 256 lanes per particle (TPP / 32 warps
 // of the block): plans with few particles, whose particles then have more
 // lanes to split their traversal slots over.  Each evaluation's sums are
@@ -15,16 +13,16 @@ constexpr int kRefineThreads = 256;  // the block size cddt_plan_refine launches
 // the same sums and takes the same step; the two halves of `red` alternate
 // between evaluations, so one barrier per evaluation suffices.
 template <typename KT, int TPP>
-__global__ void __launch_bounds__(kRefineThreads, 4)
+__global__ void __launch_bounds__(kRefineBlock, 4)
     refine_kernel_wide(const __grid_constant__ HotTable tab, const FilterDev *filters, const WorkItem *items,
                        int64_t n_items, unsigned long long *queue, int32_t steps, float eta)
 {
-    static_assert(TPP % 32 == 0 && TPP <= kRefineThreads, "whole warps of one block per particle");
+    static_assert(TPP % 32 == 0 && TPP <= kRefineBlock, "whole warps of one block per particle");
     constexpr int WPP = TPP / 32;
     extern __shared__ __align__(16) float sh[];
     __shared__ long long cur;
     __shared__ __align__(16) FilterDev F;
-    __shared__ float red[2][kRefineThreads / 32][3];
+    __shared__ float red[2][kRefineBlock / 32][3];
     const uint64_t pol = policy_evict_last();
     const int lane = threadIdx.x % TPP;
     const int group = threadIdx.x / TPP;
