@@ -19,8 +19,9 @@
 //          of its q-th child's subtree.  A search reads the header, one node
 //          per internal level and one leaf: 3 sectors for the few-hundred-key
 //          bins of a 2000 x 2000 corridor map.  Headers and internal nodes
-//          are read with an L2 evict-last policy so that the stream of leaf
-//          reads does not push them out of L2.
+//          are read with an L2 evict-last policy and leaves with an
+//          evict-first one, so that the stream of leaf reads does not push
+//          the upper levels out of L2.
 //  grid    uint8[H][W] occupancy (nonzero = occupied), edge uint8[H][W].
 //
 // Float contract: every float32 step of the projection, binning and range is
@@ -384,6 +385,18 @@ __device__ __forceinline__ uint64_t policy_evict_normal()
     return pol;
 }
 
+// Leaves are read with the evict-first priority: under a stream of leaf
+// reads that misses L2 (uniformly spread queries) they are the first lines
+// to go, ahead of the bin headers and internal nodes.
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t pol = 0;
+#if CDDT_LD_HINT
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+#endif
+    return pol;
+}
+
 // Key i of a bin from its leaf run (scalar load).
 template <typename KT>
 __device__ __forceinline__ float bin_key(const MapView &m, uint32_t off, uint32_t n, int i, float X)
@@ -672,7 +685,7 @@ __device__ __forceinline__ SearchResult tree_search(const MapView &m, uint32_t g
     }
     // leaf (loff is now the number of internal nodes)
     const char *leaf = run + ((size_t)(loff + k) << 5);
-    ld_node(chk_store(m, leaf, 32), w);
+    ld_node(chk_store(m, leaf, 32), policy_evict_first(), w);
     if constexpr (sizeof(KT) == 4) {
         uint32_t at, prev;
         bool prev_here;
