@@ -258,7 +258,9 @@ CDDT_API cddt_status cddt_plan_autotune(cddt_plan p, void *stream);
 /* Set the launch shape by hand: tpp in {1,2,4,8,16,32} threads per particle, ppi
  * particles per work item (multiple of 32 / tpp), block threads in {256,
  * 512}, regcap 0 (registers as the compiler needs) or 1 (capped so that 48
- * warps stay resident per SM).  Errors: ARG. */
+ * warps stay resident per SM).  A new shape discards a graph that
+ * cddt_plan_launch_graph captured with the old one (its next call captures
+ * again).  Errors: ARG. */
 CDDT_API cddt_status cddt_plan_set_shape(cddt_plan p, int32_t tpp, int32_t ppi, int32_t block,
                                          int32_t regcap);
 CDDT_API cddt_status cddt_plan_get_shape(cddt_plan p, int32_t *tpp, int32_t *ppi, int32_t *block,

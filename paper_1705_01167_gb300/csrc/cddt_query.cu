@@ -898,6 +898,11 @@ cddt_status cddt_plan_set_shape(cddt_plan p, int32_t tpp, int32_t ppi, int32_t b
     if (!(block == 256 || block == 512)) return CDDT_ERR_ARG;
     if (ppi < 1 || ppi % (32 / tpp)) return CDDT_ERR_ARG;
     if (regcap != 0 && regcap != 1) return CDDT_ERR_ARG;
+    if (tpp != p->tpp || ppi != p->ppi || block != p->block || regcap != p->regcap) {
+        // a graph captured with the old shape would go on launching it
+        if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+        if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+    }
     p->tpp = tpp;
     p->ppi = ppi;
     p->block = block;

@@ -93,6 +93,14 @@ def test_plan_autotune_and_graph(G, batch):
         f["logw"].fill_(float("nan"))
     plan.launch_graph()  # replay
     _check(filters, refs)
+    # a new shape drops the captured graph; the next launch captures it
+    other = dict(tpp=4 if shape["tpp"] != 4 else 8, ppi=128, block=512 if shape["block"] != 512 else 256, regcap=0)
+    plan.set_shape(**other)
+    assert plan.shape() == other
+    for f in filters:
+        f["logw"].fill_(float("nan"))
+    plan.launch_graph()
+    _check(filters, refs)
     plan.close()
 
 
