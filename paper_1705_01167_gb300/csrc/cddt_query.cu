@@ -204,13 +204,14 @@ __host__ __device__ constexpr size_t count_smem(int nbk)
 
 // Shared memory of sort_place_kernel for nbk buckets: two buffers of
 // kSortTile records (tile i's poses land in buffer i & 1 while tile i - 1 is
-// placed; its records then overwrite them, grouped by bucket), the records'
-// buckets, and per bucket the next output slot, the tile's count and its
-// first tile slot.
+// placed; its records then overwrite them, grouped by bucket), and per
+// bucket the next output slot, the tile's count, its first tile slot and
+// the difference of the two (a record at tile slot p goes to output slot
+// p + that difference).
 constexpr int kRecBuf = kSortTile * (int)sizeof(uint4);
 __host__ __device__ constexpr size_t place_smem(int nbk)
 {
-    return 2 * (size_t)kRecBuf + (size_t)kSortTile * sizeof(uint16_t) + sizeof(uint32_t) * (3 * (size_t)nbk + 1);
+    return 2 * (size_t)kRecBuf + sizeof(uint32_t) * (4 * (size_t)nbk + 1);
 }
 
 __global__ void __launch_bounds__(kSortThreads, 2) sort_place_kernel(MapView m, const float *pose, int64_t n,
@@ -219,10 +220,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_place_kernel(MapView m, 
 {
     extern __shared__ __align__(16) unsigned char smem[];
     // buffer i & 1 at smem + (i & 1) * kRecBuf: tile i's poses, then its records
-    uint16_t *tbk = reinterpret_cast<uint16_t *>(smem + 2 * kRecBuf);       // the records' buckets
-    uint32_t *cursor = reinterpret_cast<uint32_t *>(tbk + kSortTile);        // next output slot per bucket
+    uint32_t *cursor = reinterpret_cast<uint32_t *>(smem + 2 * kRecBuf);     // next output slot per bucket
     uint32_t *thist = cursor + nbk;                                          // the tile's queries per bucket
     uint32_t *toff = thist + nbk;                                            // their first tile slot; [nbk] = total
+    uint32_t *dbase = toff + nbk + 1;                                        // cursor - toff (mod 2^32)
     for (int b = threadIdx.x; b < nbk; b += blockDim.x) {
         cursor[b] = offsets[(int64_t)b * gridDim.x + blockIdx.x];
         thist[b] = 0;
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_place_kernel(MapView m, 
             for (int i = 0; i < per; ++i)
                 if (b0 + i < nbk) {
                     toff[b0 + i] = run;
+                    dbase[b0 + i] = cursor[b0 + i] - run;
                     run += thist[b0 + i];
                 }
             if (lane == 31) toff[nbk] = inc;
@@ -298,15 +300,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_place_kernel(MapView m, 
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kSortPerThread; ++j)
-            if (bk[j] >= 0) {
-                const int p = (int)toff[bk[j]] + rank[j];
-                trec[p] = r[j];
-                tbk[p] = (uint16_t)bk[j];
-            }
+            if (bk[j] >= 0) trec[(int)toff[bk[j]] + rank[j]] = r[j];
         __syncthreads();
         for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-            const int b = tbk[p];
-            rec[(size_t)cursor[b] + (size_t)(p - (int)toff[b])] = trec[p];
+            const uint4 v = trec[p];
+            // the record's bucket from its slice and direction (a non-finite
+            // heading's record has slice 0, forward: bucket 0, as counted)
+            const int b = (int)((((v.w & kRecSlice) << 1) | (v.w >> 31)) >> sh);
+            rec[(size_t)(dbase[b] + (uint32_t)p)] = v;
         }
         __syncthreads();  // the records are written out: the buffer and the counts are free
         for (int b = threadIdx.x; b < nbk; b += blockDim.x) {
