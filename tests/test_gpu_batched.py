@@ -205,3 +205,37 @@ def test_plan_on_pinned_host_buffers(G, batch):
         G.Plan([bad])
     plan.close()
     dev_plan.close()
+
+
+def test_plan_refine_lanes_and_arguments(G, batch):
+    """cddt_plan_refine over the batch's filters: with no step (one forward +
+    adjoint evaluation at the given poses) every lane count, up to a
+    particle over eight warps, gives the log-weights of cddt_plan_run and the
+    same gradients to float32 rounding of the sums; bad lane counts, steps
+    and step sizes are refused."""
+    maps, filters, refs = batch
+    fl = [dict(f, grad_xy=torch.empty((f["particles"].shape[0], 2), device="cuda"),
+               particles_out=torch.empty((f["particles"].shape[0], 3), device="cuda")) for f in filters]
+    plan = G.Plan(fl)
+    grads = {}
+    for tpp in (1, 32, 64, 128, 256, 0):
+        for f in fl:
+            f["logw"].fill_(float("nan"))
+        plan.refine(0, 0.1, tpp=tpp)
+        torch.cuda.synchronize()
+        for f, want in zip(fl, refs):
+            _close(f["logw"].cpu().numpy(), want)
+            assert torch.equal(f["particles_out"], f["particles"])  # no step: the poses stay
+        grads[tpp] = [f["grad_xy"].cpu().numpy().astype(np.float64) for f in fl]
+    for tpp, gs in grads.items():
+        for g, g1 in zip(gs, grads[1]):
+            if g1.size == 0:  # the filter without particles
+                continue
+            scale = np.maximum(np.abs(g1).max(), 1.0)
+            assert np.abs(g - g1).max() <= 1e-4 * scale, tpp
+    for bad in (dict(tpp=3), dict(tpp=512), dict(steps=-1), dict(eta=-1.0)):
+        args = dict(steps=1, eta=0.1, tpp=0)
+        args.update(bad)
+        with pytest.raises(G.CDDTError):
+            plan.refine(args["steps"], args["eta"], tpp=args["tpp"])
+    plan.close()
